@@ -1,0 +1,358 @@
+"""Seeded synthetic workload generators (graphs, edge probabilities, weights, seed sets).
+
+This module is shared by the CPU oracle's tests and by the GPU path's tests and
+benchmark.  It holds none of the diffusion method's arithmetic: it only builds
+the inputs a caller hands to ``cnd_graph_create`` / ``cnd_*_simulate`` -- a CSR
+graph, a per-edge IC probability (fp32), a per-edge LT weight (uint32 fixed
+point), and seed sets.  Every generator is a pure function of its integer
+``graph_seed`` (numpy ``Philox`` bit generator), so both sides see the same
+bytes.
+
+Workload shapes follow the paper's benchmark section (Sec. 4, "Benchmarks"):
+undirected edges become two directed edges, and the edge-weight models are
+trivalency (TV), uniformly random (UR) and weighted cascade (WC,
+p(u,v) = 1/in-degree(v)).  The LT weight for WC is the fixed-point value
+floor((2^32 - 1) / in-degree(v)), so the in-weights of a node sum to at most
+2^32 - 1 (Sec. 2, "Diffusion Models": the in-weights of a node sum to at most 1).
+"""
+from __future__ import annotations
+
+import dataclasses
+import hashlib
+
+import numpy as np
+
+__all__ = [
+    "Graph", "csr_from_edges", "erdos_renyi_m", "barabasi_albert", "rmat",
+    "random_regular", "watts_strogatz", "path_graph", "out_star", "in_star",
+    "ic_uniform", "ic_weighted_cascade", "ic_uniform_random", "ic_trivalency",
+    "lt_weighted_cascade", "top_degree_seeds", "uniform_seeds", "batch_items",
+]
+
+LT_ONE = 0xFFFFFFFF  # largest total in-weight a node may carry (fixed point "1")
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(int(seed)))
+
+
+@dataclasses.dataclass
+class Graph:
+    """Directed graph in CSR form: out-neighbours of u are col[row_ptr[u]:row_ptr[u+1]]."""
+    n: int
+    row_ptr: np.ndarray  # int32 [n+1]
+    col: np.ndarray      # int32 [m]
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.col.shape[0])
+
+    def out_degree(self) -> np.ndarray:
+        return np.diff(self.row_ptr.astype(np.int64)).astype(np.int64)
+
+    def in_degree(self) -> np.ndarray:
+        return np.bincount(self.col, minlength=self.n).astype(np.int64)
+
+    def src(self) -> np.ndarray:
+        """Source node of every edge, in CSR edge order."""
+        return np.repeat(np.arange(self.n, dtype=np.int32), self.out_degree())
+
+    def digest(self) -> str:
+        h = hashlib.sha256()
+        h.update(np.int64(self.n).tobytes())
+        h.update(np.ascontiguousarray(self.row_ptr).tobytes())
+        h.update(np.ascontiguousarray(self.col).tobytes())
+        return h.hexdigest()[:16]
+
+
+def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, name: str = "",
+                   sort: bool = True) -> Graph:
+    """CSR from an edge list.  With ``sort`` the edges of a row are ordered by target."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    if sort:
+        order = np.lexsort((dst, src))
+    else:
+        order = np.argsort(src, kind="stable")
+    src = src[order]
+    dst = dst[order]
+    counts = np.bincount(src, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    if row_ptr[-1] > np.iinfo(np.int32).max:
+        raise ValueError("edge count exceeds int32")
+    return Graph(n=n, row_ptr=row_ptr.astype(np.int32), col=dst.astype(np.int32), name=name)
+
+
+def _dedup_keys(keys: np.ndarray) -> np.ndarray:
+    keys.sort()
+    if keys.size == 0:
+        return keys
+    keep = np.empty(keys.size, dtype=bool)
+    keep[0] = True
+    np.not_equal(keys[1:], keys[:-1], out=keep[1:])
+    return keys[keep]
+
+
+def erdos_renyi_m(n: int, m: int, graph_seed: int = 1) -> Graph:
+    """Directed G(n, m): m distinct edges with uniform endpoints and no self-loops.
+
+    Duplicates and self-loops are dropped and redrawn until exactly m distinct
+    edges remain (first occurrence kept, in draw order).
+    """
+    if m > n * (n - 1):
+        raise ValueError("too many edges")
+    rng = _rng(graph_seed)
+    chosen = np.empty(0, dtype=np.int64)
+    seen: set = set()
+    out = []
+    while len(out) < m:
+        need = m - len(out)
+        s = rng.integers(0, n, size=2 * need + 16, dtype=np.int64)
+        d = rng.integers(0, n, size=2 * need + 16, dtype=np.int64)
+        for a, b in zip(s.tolist(), d.tolist()):
+            if a == b:
+                continue
+            k = a * n + b
+            if k in seen:
+                continue
+            seen.add(k)
+            out.append(k)
+            if len(out) == m:
+                break
+    chosen = np.array(out, dtype=np.int64)
+    return csr_from_edges(n, chosen // n, chosen % n, name=f"er_n{n}_m{m}")
+
+
+def barabasi_albert(n: int, m_attach: int, graph_seed: int = 1) -> Graph:
+    """Barabasi-Albert preferential attachment, each undirected edge stored both ways.
+
+    Nodes 0..m_attach-1 start unconnected; node m_attach links to all of them;
+    every later node links to m_attach distinct earlier nodes drawn with
+    probability proportional to degree (uniform draws from the list of edge
+    endpoints).  Undirected edges: (n - m_attach) * m_attach.
+    """
+    if not (1 <= m_attach < n):
+        raise ValueError("need 1 <= m_attach < n")
+    rng = _rng(graph_seed)
+    n_und = (n - m_attach) * m_attach
+    ends = np.empty(2 * n_und, dtype=np.int64)  # endpoint multiset, grows as edges are added
+    e_src = np.empty(n_und, dtype=np.int64)
+    e_dst = np.empty(n_und, dtype=np.int64)
+    filled = 0
+    targets = list(range(m_attach))
+    pool = rng.integers(0, 1 << 62, size=1 << 16, dtype=np.int64)
+    pi = 0
+    for v in range(m_attach, n):
+        base = filled
+        for t in targets:
+            e_src[filled] = v
+            e_dst[filled] = t
+            ends[2 * filled] = v
+            ends[2 * filled + 1] = t
+            filled += 1
+        if v + 1 == n:
+            break
+        size = 2 * filled
+        picked: list = []
+        while len(picked) < m_attach:
+            if pi == pool.size:
+                pool = rng.integers(0, 1 << 62, size=1 << 16, dtype=np.int64)
+                pi = 0
+            cand = int(ends[int(pool[pi]) % size])
+            pi += 1
+            if cand not in picked:
+                picked.append(cand)
+        targets = picked
+        del base
+    src = np.concatenate([e_src, e_dst])
+    dst = np.concatenate([e_dst, e_src])
+    return csr_from_edges(n, src, dst, name=f"ba_n{n}_m{m_attach}")
+
+
+def rmat(scale: int, n_samples: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+         graph_seed: int = 1, chunk: int = 1 << 23) -> Graph:
+    """R-MAT graph on n = 2^scale nodes from ``n_samples`` edge samples.
+
+    Each sample descends ``scale`` levels of the adjacency matrix, choosing the
+    quadrant (a: top-left, b: top-right, c: bottom-left, d: bottom-right) with
+    the given probabilities.  Probabilities are taken in units of 1/100, so the
+    usual (.57, .19, .19, .05) split is drawn exactly.  Self-loops and
+    duplicate edges are dropped, so m <= n_samples.
+    """
+    n = 1 << scale
+    pa, pb, pc = int(round(a * 100)), int(round(b * 100)), int(round(c * 100))
+    if min(pa, pb, pc) < 0 or pa + pb + pc > 100:
+        raise ValueError("bad quadrant probabilities")
+    rng = _rng(graph_seed)
+    parts = []
+    done = 0
+    while done < n_samples:
+        k = min(chunk, n_samples - done)
+        s = np.zeros(k, dtype=np.int64)
+        d = np.zeros(k, dtype=np.int64)
+        for lvl in range(scale):
+            r = rng.integers(0, 100, size=k, dtype=np.uint8)
+            sbit = (r >= pa + pb).astype(np.int64)                       # c or d
+            dbit = (((r >= pa) & (r < pa + pb)) | (r >= pa + pb + pc)).astype(np.int64)  # b or d
+            shift = scale - 1 - lvl
+            s |= sbit << shift
+            d |= dbit << shift
+        keep = s != d
+        parts.append((s[keep] << 32) | d[keep])
+        done += k
+    keys = _dedup_keys(np.concatenate(parts))
+    src = (keys >> 32).astype(np.int64)
+    dst = (keys & 0xFFFFFFFF).astype(np.int64)
+    # keys are sorted by (src, dst): CSR order already
+    counts = np.bincount(src, minlength=n)
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=row_ptr[1:])
+    return Graph(n=n, row_ptr=row_ptr.astype(np.int32), col=dst.astype(np.int32),
+                 name=f"rmat_s{scale}_{n_samples}")
+
+
+def random_regular(n: int, d: int, graph_seed: int = 1, max_tries: int = 1000) -> Graph:
+    """Random d-regular simple undirected graph (pairing model with restarts), both directions stored."""
+    if (n * d) % 2:
+        raise ValueError("n*d must be even")
+    rng = _rng(graph_seed)
+    for _ in range(max_tries):
+        stubs = np.repeat(np.arange(n, dtype=np.int64), d)
+        rng.shuffle(stubs)
+        u = stubs[0::2]
+        v = stubs[1::2]
+        if np.any(u == v):
+            continue
+        lo = np.minimum(u, v)
+        hi = np.maximum(u, v)
+        k = lo * n + hi
+        if np.unique(k).size != k.size:
+            continue
+        src = np.concatenate([u, v])
+        dst = np.concatenate([v, u])
+        return csr_from_edges(n, src, dst, name=f"rr_n{n}_d{d}")
+    raise RuntimeError("pairing model did not produce a simple graph")
+
+
+def watts_strogatz(n: int, k: int, p: float, graph_seed: int = 1) -> Graph:
+    """Watts-Strogatz small world (ring lattice with k/2 neighbours each side, rewiring p), both directions stored."""
+    rng = _rng(graph_seed)
+    half = k // 2
+    edges = set()
+    for u in range(n):
+        for j in range(1, half + 1):
+            v = (u + j) % n
+            edges.add((min(u, v), max(u, v)))
+    edge_list = sorted(edges)
+    adj = {e for e in edge_list}
+    out = []
+    for (u, v) in edge_list:
+        if rng.random() < p:
+            for _ in range(64):
+                w = int(rng.integers(0, n))
+                e = (min(u, w), max(u, w))
+                if w != u and e not in adj:
+                    adj.discard((u, v))
+                    adj.add(e)
+                    u, v = e
+                    break
+        out.append((u, v))
+    arr = np.array(sorted(adj), dtype=np.int64)
+    src = np.concatenate([arr[:, 0], arr[:, 1]])
+    dst = np.concatenate([arr[:, 1], arr[:, 0]])
+    return csr_from_edges(n, src, dst, name=f"ws_n{n}_k{k}")
+
+
+def path_graph(length: int) -> Graph:
+    """Directed path 0 -> 1 -> ... -> length (length edges)."""
+    n = length + 1
+    src = np.arange(length, dtype=np.int64)
+    return csr_from_edges(n, src, src + 1, name=f"path{length}")
+
+
+def out_star(k: int) -> Graph:
+    """Centre 0 with edges 0 -> 1..k."""
+    return csr_from_edges(k + 1, np.zeros(k, dtype=np.int64), np.arange(1, k + 1), name=f"ostar{k}")
+
+
+def in_star(k: int) -> Graph:
+    """Leaves 1..k with edges leaf -> 0."""
+    return csr_from_edges(k + 1, np.arange(1, k + 1), np.zeros(k, dtype=np.int64), name=f"istar{k}")
+
+
+# ---------------------------------------------------------------- edge weights
+def ic_uniform(g: Graph, p: float) -> np.ndarray:
+    return np.full(g.m, np.float32(p), dtype=np.float32)
+
+
+def ic_weighted_cascade(g: Graph) -> np.ndarray:
+    """p(u,v) = 1/in-degree(v), one IEEE fp32 division per edge."""
+    indeg = g.in_degree().astype(np.float32)
+    return (np.float32(1.0) / indeg[g.col]).astype(np.float32)
+
+
+def ic_uniform_random(g: Graph, hi: float = 1.0, graph_seed: int = 1) -> np.ndarray:
+    """p ~ U[0, hi) in fp32 per edge (UR model; hi=0.1 for the batched R-MAT workload)."""
+    rng = _rng(graph_seed + 0x5EED)
+    return (rng.random(g.m, dtype=np.float32) * np.float32(hi)).astype(np.float32)
+
+
+def ic_trivalency(g: Graph, graph_seed: int = 1) -> np.ndarray:
+    """p drawn uniformly from {0.1, 0.01, 0.001} per edge (TV model)."""
+    rng = _rng(graph_seed + 0x7EED)
+    vals = np.array([0.1, 0.01, 0.001], dtype=np.float32)
+    return vals[rng.integers(0, 3, size=g.m)]
+
+
+def lt_weighted_cascade(g: Graph) -> np.ndarray:
+    """LT weight of (u,v) = floor((2^32-1)/in-degree(v)) as uint32 (in-weights sum <= 2^32-1)."""
+    indeg = g.in_degree()
+    w = np.zeros(g.n, dtype=np.uint64)
+    nz = indeg > 0
+    w[nz] = np.uint64(LT_ONE) // indeg[nz].astype(np.uint64)
+    return w[g.col].astype(np.uint32)
+
+
+# ---------------------------------------------------------------- seed sets
+def top_degree_seeds(g: Graph, k: int) -> np.ndarray:
+    """k nodes of largest out-degree, ties broken by lower node id."""
+    deg = g.out_degree()
+    order = np.lexsort((np.arange(g.n), -deg))
+    return order[:k].astype(np.int32)
+
+
+def uniform_seeds(n: int, k: int, rng_or_seed) -> np.ndarray:
+    """k distinct nodes drawn uniformly (order of first draw kept)."""
+    rng = rng_or_seed if isinstance(rng_or_seed, np.random.Generator) else _rng(rng_or_seed)
+    if k > n:
+        raise ValueError("k > n")
+    out: list = []
+    seen: set = set()
+    while len(out) < k:
+        for x in rng.integers(0, n, size=2 * (k - len(out)) + 4).tolist():
+            if x not in seen:
+                seen.add(x)
+                out.append(x)
+                if len(out) == k:
+                    break
+    return np.array(out, dtype=np.int32)
+
+
+def batch_items(n: int, n_items: int, size_lo: int, size_hi: int, trial_choices,
+                graph_seed: int = 1):
+    """Batched-simulation items: (seed_off[n_items+1] int64, seeds int32, n_trials int32, rng_seed uint64).
+
+    Seed-set sizes are uniform on {size_lo..size_hi}; each set holds distinct
+    uniform nodes; trial counts are uniform over ``trial_choices``; item i uses
+    rng_seed i+1.
+    """
+    rng = _rng(graph_seed + 0xBA7C)
+    sizes = rng.integers(size_lo, size_hi + 1, size=n_items)
+    trials = np.asarray(trial_choices, dtype=np.int32)[rng.integers(0, len(trial_choices), size=n_items)]
+    seed_off = np.zeros(n_items + 1, dtype=np.int64)
+    np.cumsum(sizes, out=seed_off[1:])
+    seeds = np.concatenate([uniform_seeds(n, int(s), rng) for s in sizes]) if n_items else np.zeros(0, np.int32)
+    rng_seeds = np.arange(1, n_items + 1, dtype=np.uint64)
+    return seed_off, seeds.astype(np.int32), trials.astype(np.int32), rng_seeds
