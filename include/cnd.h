@@ -1,0 +1,177 @@
+/*
+ * cnd.h -- C ABI of the GB300 (sm_103a) Monte Carlo engine for the independent
+ * cascade (IC) and linear threshold (LT) diffusion models.
+ *
+ * The models are the ones stated in CyNetDiff (arXiv 2404.17059), Sec. 2
+ * "Diffusion Models"; the graph is a directed CSR graph (Sec. 3 "Data
+ * Structures"); the quantity estimated is sigma(S), the expected number of
+ * active nodes when the process started from seed set S stops (Sec. 2
+ * "Influence Maximization").  One call runs many independent trials from one
+ * seed set and reports, per trial, how many nodes ended active (the spread)
+ * and, per node, in how many trials it ended active (the data of the paper's
+ * activation heatmap, Sec. 4 "Visualizations").
+ *
+ * Definitions that bind every entry point (the paper fixes no random number
+ * generator or rounding; these are this library's readings):
+ *
+ *   Random numbers.  Philox4x32-10 (Salmon et al., SC'11) with key
+ *   (lo32(rng_seed), hi32(rng_seed)).  For trial t let g = t >> 2, j = t & 3:
+ *     IC coin of edge e      = Philox(e, lo32(g), 0, hi32(g))[j]
+ *     LT threshold of node v = Philox(v, lo32(g), 1, hi32(g))[j]
+ *   e is the position of the edge in the caller's `col` array.  A trial is
+ *   therefore a pure function of (graph, seeds, rng_seed, t): results do not
+ *   depend on how trials are grouped, on traversal order or on direction.
+ *
+ *   IC.  Probability p (fp32, 0 <= p <= 1) becomes the threshold
+ *   thr = floor(p * 2^32) for p < 1 and thr = 0xFFFFFFFF ("always") for
+ *   p == 1.  Edge e is live in trial t iff thr == 0xFFFFFFFF or coin < thr, so
+ *   its live probability is exactly thr / 2^32.  Because every edge's coin is
+ *   fixed per trial, the set of active nodes is the set reachable from S over
+ *   live edges (each newly active node gets one chance per inactive
+ *   out-neighbour, Sec. 2).
+ *
+ *   LT.  Weights are uint32 fixed point: the weight w of edge u->v is the
+ *   influence of u on v, and for every node the in-weights sum to at most
+ *   2^32 - 1 (the fixed-point form of "sum <= 1", Sec. 2).  Node v becomes
+ *   active in the step after the total weight of its active in-neighbours
+ *   exceeds its threshold theta (a uint32): activation probability given total
+ *   W is exactly W / 2^32, and a node with no active in-weight never activates.
+ *
+ *   Steps.  Seeds are active at step 0 (duplicates count once); a node
+ *   activated at step L+1 has an in-neighbour activated at step L (Sec. 3,
+ *   Observation 1).  Expansion is level-synchronous, so a node's step is its
+ *   activation time in the paper's process.
+ *
+ *   Spread counts the seeds.  Edge checks (throughput unit) = sum over trials
+ *   of sum over active nodes of out-degree: every active node examines its
+ *   out-row once per trial (Sec. 3 "Algorithms": work proportional to the
+ *   edges incident to activated nodes).
+ *
+ * Conventions.  Inputs are copied: the caller keeps ownership of its arrays.
+ * Outputs are caller-allocated.  Unless `device_ptrs` is set in the options,
+ * seeds and outputs are host pointers and the call returns after the results
+ * are written.  Every function returns a cnd_status; on failure
+ * cnd_last_error() describes the failure in a thread-local string.  Calls on
+ * one graph from several host threads are allowed when they use distinct
+ * streams.  Nothing here falls back to the CPU.
+ */
+#ifndef CND_H
+#define CND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cnd_graph cnd_graph; /* opaque; device copy owned by the library */
+typedef int32_t cnd_status;
+
+#define CND_OK 0
+#define CND_EINVAL (-1)    /* bad argument or malformed graph */
+#define CND_ENOMEM (-2)    /* device or host allocation failed */
+#define CND_ECUDA (-3)     /* CUDA runtime error (no device, launch failure, ...) */
+#define CND_ELIMIT (-4)    /* some trial still had newly active nodes at step max_levels */
+#define CND_ETIMEOUT (-5)  /* host watchdog expired; outputs are not valid */
+#define CND_EOVERFLOW (-6) /* LT in-weights of a node sum above 2^32 - 1 */
+
+#define CND_DIR_AUTO 0 /* push or pull per step, by frontier size */
+#define CND_DIR_PUSH 1
+#define CND_DIR_PULL 2
+
+/* Options of the *_ex entry points.  Zero-initialise (cnd_sim_opts_init). */
+typedef struct cnd_sim_opts {
+    int64_t first_trial;       /* id of the first trial; a multiple of 64 (default 0) */
+    int32_t max_levels;        /* <= 0: no cap; else steps 1..max_levels are expanded and
+                                  a node activated at step max_levels yields CND_ELIMIT
+                                  (outputs are still written) */
+    int32_t direction;         /* CND_DIR_* */
+    int32_t word_bits;         /* trials held per node per pass: 0 = automatic, else a multiple
+                                  of 64 up to 16384 */
+    int32_t device_ptrs;       /* 1: seeds and all outputs are device pointers, and the call
+                                  only enqueues work on `stream` */
+    void *stream;              /* cudaStream_t to run on; NULL = legacy default stream */
+    int64_t *edge_checks_out;  /* NULL or 1 value: edge checks summed over the trials */
+    int64_t *level_counts_out; /* NULL or level_counts_len values: [L] = number of
+                                  (trial, node) pairs activated at step L */
+    int32_t level_counts_len;
+    int32_t pull_permille;     /* AUTO: pull when the frontier's out-edges exceed this many
+                                  thousandths of m; 0 = built-in default */
+    int32_t chunk_edges;       /* edges per push work item (0 = automatic) */
+    int32_t reserved0;
+    double timeout_s;          /* > 0: give up with CND_ETIMEOUT after this many seconds */
+    int64_t reserved[4];
+} cnd_sim_opts;
+
+void cnd_sim_opts_init(cnd_sim_opts *opts);
+
+/*
+ * Build the device copy of a directed CSR graph (Sec. 3 "Data Structures":
+ * out-neighbours of u are col[row_ptr[u] .. row_ptr[u+1]-1]).
+ *   n > 0 nodes, m >= 0 edges; row_ptr has n+1 entries, row_ptr[0] = 0,
+ *   non-decreasing, row_ptr[n] = m; 0 <= col[e] < n.
+ *   ic_prob: m fp32 IC probabilities in [0, 1] (NaN rejected), or NULL if the
+ *            graph is only used for LT.
+ *   lt_weight_fx: m uint32 LT weights, in-weights of every node summing to at
+ *            most 2^32 - 1 (else CND_EOVERFLOW), or NULL if only used for IC.
+ *   Self-loops and parallel edges are accepted.  All arrays are host memory
+ *   and are copied.  The graph lives on the device that is current.
+ *   *out receives the handle (NULL on failure).
+ */
+cnd_status cnd_graph_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col,
+                            const float *ic_prob, const uint32_t *lt_weight_fx, cnd_graph **out);
+
+/* Release a graph (NULL-safe).  No call on it may be in flight. */
+void cnd_graph_destroy(cnd_graph *g);
+
+/* n, m and which models the graph carries (any output may be NULL). */
+cnd_status cnd_graph_info(const cnd_graph *g, int32_t *n, int32_t *m, int32_t *has_ic, int32_t *has_lt);
+
+/*
+ * Monte Carlo IC simulation (Sec. 2 "Diffusion Models", first model): trials
+ * 0 .. n_trials-1 from seed set `seeds` (n_seeds ids in [0, n); duplicates
+ * count once; n_seeds = 0 gives spread 0).
+ *   spread_out:     NULL or n_trials int32, spread of each trial.
+ *   node_count_out: NULL or n int32, number of trials in which each node is active.
+ * 0 <= n_trials <= 2^31 - 1.  CND_EINVAL if the graph carries no IC probabilities.
+ */
+cnd_status cnd_ic_simulate(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                           uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out);
+
+/* Monte Carlo LT simulation (Sec. 2, second model); arguments as cnd_ic_simulate.
+ * CND_EINVAL if the graph carries no LT weights. */
+cnd_status cnd_lt_simulate(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                           uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out);
+
+/* As above with options (opts may be NULL = defaults).  Trial ids run from
+ * opts->first_trial; spread_out[i] is trial first_trial + i. */
+cnd_status cnd_ic_simulate_ex(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                              uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out,
+                              const cnd_sim_opts *opts);
+cnd_status cnd_lt_simulate_ex(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                              uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out,
+                              const cnd_sim_opts *opts);
+
+/*
+ * Weighted-cascade LT weights for a CSR graph (Sec. 4 "Benchmarks", WC model:
+ * the weight of every edge entering v is 1/in-degree(v)) in fixed point:
+ * w_out[e] = floor((2^32 - 1) / in-degree(col[e])), so in-weights sum to at
+ * most 2^32 - 1.  Host arrays: col has m entries in [0, n), w_out m entries.
+ */
+cnd_status cnd_lt_weights_wc(int32_t n, int32_t m, const int32_t *col, uint32_t *w_out);
+
+/*
+ * The engine's device Philox4x32-10 (the generator defined above), for
+ * checking: out[4i..4i+3] = Philox(ctr[4i..4i+3]) under key rng_seed, for
+ * i < count.  Host arrays of 4*count uint32 each.
+ */
+cnd_status cnd_philox4x32_10(uint64_t rng_seed, const uint32_t *ctr, int64_t count, uint32_t *out);
+
+/* Message describing the last failure on this host thread ("" if none). */
+const char *cnd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CND_H */

@@ -1,0 +1,263 @@
+"""Thin ctypes binding of libcnd (include/cnd.h): argument marshalling only.
+
+Every simulation step runs in the library's CUDA kernels.  Host numpy arrays
+are passed as host pointers; torch CUDA tensors are passed as device pointers
+(``device_ptrs = 1``) together with torch's current stream.  There is no CPU
+fallback: if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+CND_OK, CND_EINVAL, CND_ENOMEM, CND_ECUDA, CND_ELIMIT, CND_ETIMEOUT, CND_EOVERFLOW = 0, -1, -2, -3, -4, -5, -6
+CND_DIR_AUTO, CND_DIR_PUSH, CND_DIR_PULL = 0, 1, 2
+_DIRS = {"auto": CND_DIR_AUTO, "push": CND_DIR_PUSH, "pull": CND_DIR_PULL}
+
+# every symbol include/cnd.h declares
+EXPORTS = (
+    "cnd_sim_opts_init", "cnd_graph_create", "cnd_graph_destroy", "cnd_graph_info", "cnd_ic_simulate",
+    "cnd_lt_simulate", "cnd_ic_simulate_ex", "cnd_lt_simulate_ex", "cnd_lt_weights_wc",
+    "cnd_philox4x32_10", "cnd_last_error",
+)
+
+
+class CndError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"cnd status {status}: {msg}")
+        self.status = status
+
+
+class cnd_sim_opts(C.Structure):
+    _fields_ = [
+        ("first_trial", C.c_int64),
+        ("max_levels", C.c_int32),
+        ("direction", C.c_int32),
+        ("word_bits", C.c_int32),
+        ("device_ptrs", C.c_int32),
+        ("stream", C.c_void_p),
+        ("edge_checks_out", C.c_void_p),
+        ("level_counts_out", C.c_void_p),
+        ("level_counts_len", C.c_int32),
+        ("pull_permille", C.c_int32),
+        ("chunk_edges", C.c_int32),
+        ("reserved0", C.c_int32),
+        ("timeout_s", C.c_double),
+        ("reserved", C.c_int64 * 4),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcnd.so (building it with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libcnd not built: {path} is missing")
+            _build.build()
+        L = C.CDLL(path)
+        vp, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+        L.cnd_sim_opts_init.argtypes = [vp]
+        L.cnd_sim_opts_init.restype = None
+        L.cnd_graph_create.argtypes = [i32, i32, vp, vp, vp, vp, C.POINTER(vp)]
+        L.cnd_graph_create.restype = i32
+        L.cnd_graph_destroy.argtypes = [vp]
+        L.cnd_graph_destroy.restype = None
+        L.cnd_graph_info.argtypes = [vp, vp, vp, vp, vp]
+        L.cnd_graph_info.restype = i32
+        for name in ("cnd_ic_simulate", "cnd_lt_simulate"):
+            getattr(L, name).argtypes = [vp, vp, i32, i64, u64, vp, vp]
+            getattr(L, name).restype = i32
+        for name in ("cnd_ic_simulate_ex", "cnd_lt_simulate_ex"):
+            getattr(L, name).argtypes = [vp, vp, i32, i64, u64, vp, vp, C.POINTER(cnd_sim_opts)]
+            getattr(L, name).restype = i32
+        L.cnd_lt_weights_wc.argtypes = [i32, i32, vp, vp]
+        L.cnd_lt_weights_wc.restype = i32
+        L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
+        L.cnd_philox4x32_10.restype = i32
+        L.cnd_last_error.argtypes = []
+        L.cnd_last_error.restype = C.c_char_p
+        _lib = L
+        return L
+
+
+def cnd_last_error() -> str:
+    return load().cnd_last_error().decode()
+
+
+def _check(st: int, allow=()):
+    if st < 0 and st not in allow:
+        raise CndError(st, cnd_last_error())
+    return st
+
+
+def _np_ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _is_torch_cuda(x) -> bool:
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def cnd_sim_opts_init() -> cnd_sim_opts:
+    o = cnd_sim_opts()
+    load().cnd_sim_opts_init(C.byref(o))
+    return o
+
+
+class CndGraph:
+    """Owning handle of a cnd_graph (destroyed with the object)."""
+
+    def __init__(self, handle, n, m, has_ic, has_lt):
+        self.handle = handle
+        self.n, self.m, self.has_ic, self.has_lt = n, m, has_ic, has_lt
+
+    def __del__(self):
+        h, self.handle = getattr(self, "handle", None), None
+        if h and _lib is not None:
+            _lib.cnd_graph_destroy(h)
+
+    def close(self):
+        self.__del__()
+
+
+def cnd_graph_create(n, row_ptr, col, ic_prob=None, lt_weight_fx=None) -> CndGraph:
+    L = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    icp = None if ic_prob is None else np.ascontiguousarray(ic_prob, dtype=np.float32)
+    ltw = None if lt_weight_fx is None else np.ascontiguousarray(lt_weight_fx, dtype=np.uint32)
+    m = int(col.shape[0])
+    out = C.c_void_p()
+    _check(L.cnd_graph_create(int(n), m, _np_ptr(row_ptr), _np_ptr(col), _np_ptr(icp), _np_ptr(ltw), C.byref(out)))
+    return CndGraph(out, int(n), m, icp is not None, ltw is not None)
+
+
+def cnd_graph_destroy(g: CndGraph) -> None:
+    g.close()
+
+
+def cnd_graph_info(g: CndGraph):
+    n, m, hi, hl = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().cnd_graph_info(g.handle, C.byref(n), C.byref(m), C.byref(hi), C.byref(hl)))
+    return n.value, m.value, bool(hi.value), bool(hl.value)
+
+
+@dataclasses.dataclass
+class SimResult:
+    status: int
+    spread: object = None        # int32 [n_trials]
+    node_count: object = None    # int32 [n]
+    edge_checks: int | None = None
+    level_counts: object = None  # int64 [level_counts_len]
+
+
+def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=True, node_count=True,
+              first_trial=0, max_levels=0, direction="auto", word_bits=0, level_counts_len=0,
+              edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None):
+    L = load()
+    n_trials = int(n_trials)
+    dev = _is_torch_cuda(seeds)
+    if dev:
+        import torch
+        seeds_t = seeds.to(torch.int32).contiguous()
+        sp = torch.empty(n_trials, dtype=torch.int32, device=seeds.device) if spread else None
+        nc = torch.empty(g.n, dtype=torch.int32, device=seeds.device) if node_count else None
+        ec = torch.zeros(1, dtype=torch.int64, device=seeds.device) if edge_checks else None
+        lc = torch.zeros(level_counts_len, dtype=torch.int64, device=seeds.device) if level_counts_len else None
+        seeds_p = C.c_void_p(seeds_t.data_ptr()) if seeds_t.numel() else None
+        n_seeds = seeds_t.numel()
+        sp_p = C.c_void_p(sp.data_ptr()) if sp is not None and n_trials else None
+        nc_p = C.c_void_p(nc.data_ptr()) if nc is not None else None
+        ec_p = ec.data_ptr() if ec is not None else None
+        lc_p = lc.data_ptr() if lc is not None else None
+        strm = stream if stream is not None else torch.cuda.current_stream(seeds.device).cuda_stream
+    else:
+        seeds_a = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).ravel())
+        sp = np.empty(n_trials, dtype=np.int32) if spread else None
+        nc = np.empty(g.n, dtype=np.int32) if node_count else None
+        ec = np.zeros(1, dtype=np.int64) if edge_checks else None
+        lc = np.zeros(level_counts_len, dtype=np.int64) if level_counts_len else None
+        seeds_p = _np_ptr(seeds_a) if seeds_a.size else None
+        n_seeds = seeds_a.size
+        sp_p = _np_ptr(sp) if sp is not None and n_trials else None
+        nc_p = _np_ptr(nc)
+        ec_p = ec.ctypes.data if ec is not None else None
+        lc_p = lc.ctypes.data if lc is not None else None
+        strm = stream
+    if ex:
+        o = cnd_sim_opts_init()
+        o.first_trial = int(first_trial)
+        o.max_levels = int(max_levels)
+        o.direction = _DIRS[direction] if isinstance(direction, str) else int(direction)
+        o.word_bits = int(word_bits)
+        o.device_ptrs = 1 if dev else 0
+        o.stream = strm
+        o.edge_checks_out = ec_p
+        o.level_counts_out = lc_p
+        o.level_counts_len = int(level_counts_len)
+        o.pull_permille = int(pull_permille)
+        o.chunk_edges = int(chunk_edges)
+        o.timeout_s = float(timeout_s)
+        st = getattr(L, fn_name)(g.handle, seeds_p, int(n_seeds), n_trials, C.c_uint64(rng_seed), sp_p, nc_p,
+                                 C.byref(o))
+    else:
+        if dev:
+            raise ValueError(f"{fn_name} takes host arrays; use the _ex form for device tensors")
+        st = getattr(L, fn_name)(g.handle, seeds_p, int(n_seeds), n_trials, C.c_uint64(rng_seed), sp_p, nc_p)
+    _check(st, allow=(CND_ELIMIT,))
+    ecv = None
+    if ec is not None:
+        ecv = int(ec[0].item()) if dev else int(ec[0])
+    return SimResult(st, sp, nc, ecv, lc)
+
+
+def cnd_ic_simulate(g, seeds, n_trials, rng_seed, *, spread=True, node_count=True) -> SimResult:
+    return _simulate("cnd_ic_simulate", g, seeds, n_trials, rng_seed, ex=False, spread=spread, node_count=node_count)
+
+
+def cnd_lt_simulate(g, seeds, n_trials, rng_seed, *, spread=True, node_count=True) -> SimResult:
+    return _simulate("cnd_lt_simulate", g, seeds, n_trials, rng_seed, ex=False, spread=spread, node_count=node_count)
+
+
+def cnd_ic_simulate_ex(g, seeds, n_trials, rng_seed, **kw) -> SimResult:
+    return _simulate("cnd_ic_simulate_ex", g, seeds, n_trials, rng_seed, ex=True, **kw)
+
+
+def cnd_lt_simulate_ex(g, seeds, n_trials, rng_seed, **kw) -> SimResult:
+    return _simulate("cnd_lt_simulate_ex", g, seeds, n_trials, rng_seed, ex=True, **kw)
+
+
+def cnd_lt_weights_wc(n, col) -> np.ndarray:
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    w = np.empty(col.shape[0], dtype=np.uint32)
+    _check(load().cnd_lt_weights_wc(int(n), int(col.shape[0]), _np_ptr(col), _np_ptr(w)))
+    return w
+
+
+def cnd_philox4x32_10(rng_seed, ctr) -> np.ndarray:
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    _check(load().cnd_philox4x32_10(C.c_uint64(rng_seed), _np_ptr(ctr), int(ctr.shape[0]), _np_ptr(out)))
+    return out

@@ -1,0 +1,291 @@
+// Graph ingest (CSR upload, IC probability -> threshold, LT weights, in-CSR),
+// option defaults, error strings and the device Philox check entry point.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <vector>
+
+#include "cnd_common.cuh"
+
+namespace cnd {
+
+static thread_local char g_err[1024] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+// IC probability -> fixed-point threshold (floor(p * 2^32), p == 1 -> always).
+// p * 2^32 is exact in fp32 (a power-of-two scaling of a value below 1 stays
+// below 2^32), and the float -> uint conversion truncates, i.e. floors.
+__global__ void k_build_ic_edges(int32_t m, const int32_t *__restrict__ col, const float *__restrict__ p,
+                                 uint2 *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const float x = p[e];
+        const uint32_t thr = (x == 1.0f) ? kAlways : __float2uint_rz(x * 4294967296.0f);
+        out[e] = make_uint2((uint32_t)col[e], thr);
+    }
+}
+
+__global__ void k_build_lt_edges(int32_t m, const int32_t *__restrict__ col, const uint32_t *__restrict__ w,
+                                 uint2 *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = make_uint2((uint32_t)col[e], w[e]);
+}
+
+// in_edge[k] = {src, edge id, IC threshold, LT weight} for the k-th in-edge.
+__global__ void k_build_in_edges(int32_t m, const int32_t *__restrict__ in_src, const int32_t *__restrict__ in_eid,
+                                 const uint2 *__restrict__ ic, const uint2 *__restrict__ lt, uint4 *__restrict__ out) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < m; k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = in_eid[k];
+        out[k] = make_uint4((uint32_t)in_src[k], (uint32_t)e, ic ? ic[e].y : 0u, lt ? lt[e].y : 0u);
+    }
+}
+
+__global__ void k_philox(uint32_t k0, uint32_t k1, const uint4 *__restrict__ ctr, int64_t count, uint4 *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 c = ctr[i];
+        const U4 r = philox4x32_10(c.x, c.y, c.z, c.w, k0, k1);
+        out[i] = make_uint4(r.x, r.y, r.z, r.w);
+    }
+}
+
+static void free_dev(cnd_graph_dev &d) {
+    cudaFree(d.row_ptr);
+    cudaFree(d.ic_edge);
+    cudaFree(d.lt_edge);
+    cudaFree(d.in_row_ptr);
+    cudaFree(d.in_edge);
+    d = cnd_graph_dev{};
+}
+
+}  // namespace cnd
+
+using namespace cnd;
+
+extern "C" {
+
+const char *cnd_last_error(void) { return g_err; }
+
+void cnd_sim_opts_init(cnd_sim_opts *o) {
+    if (o) memset(o, 0, sizeof(*o));
+}
+
+cnd_status cnd_lt_weights_wc(int32_t n, int32_t m, const int32_t *col, uint32_t *w_out) {
+    clear_error();
+    if (n <= 0 || m < 0 || (m > 0 && (!col || !w_out))) {
+        set_error("cnd_lt_weights_wc: bad arguments");
+        return CND_EINVAL;
+    }
+    std::vector<int64_t> indeg((size_t)n, 0);
+    for (int64_t e = 0; e < m; ++e) {
+        if (col[e] < 0 || col[e] >= n) {
+            set_error("cnd_lt_weights_wc: col[%lld] out of range", (long long)e);
+            return CND_EINVAL;
+        }
+        indeg[col[e]]++;
+    }
+    for (int64_t e = 0; e < m; ++e) w_out[e] = (uint32_t)(0xFFFFFFFFull / (uint64_t)indeg[col[e]]);
+    return CND_OK;
+}
+
+cnd_status cnd_graph_create(int32_t n, int32_t m, const int32_t *row_ptr, const int32_t *col, const float *ic_prob,
+                            const uint32_t *lt_weight_fx, cnd_graph **out) {
+    clear_error();
+    if (!out) {
+        set_error("cnd_graph_create: out is NULL");
+        return CND_EINVAL;
+    }
+    *out = nullptr;
+    // ---- host-side validation: nothing touches the device before the input is known good
+    if (n <= 0 || m < 0 || !row_ptr || (m > 0 && !col)) {
+        set_error("cnd_graph_create: need n > 0, m >= 0, row_ptr and col");
+        return CND_EINVAL;
+    }
+    if (row_ptr[0] != 0 || row_ptr[n] != m) {
+        set_error("cnd_graph_create: row_ptr[0] must be 0 and row_ptr[n] must equal m");
+        return CND_EINVAL;
+    }
+    int32_t max_deg = 0;
+    for (int32_t u = 0; u < n; ++u) {
+        const int32_t d = row_ptr[u + 1] - row_ptr[u];
+        if (d < 0) {
+            set_error("cnd_graph_create: row_ptr decreases at node %d", u);
+            return CND_EINVAL;
+        }
+        if (d > max_deg) max_deg = d;
+    }
+    std::vector<int64_t> indeg((size_t)n, 0);
+    for (int32_t e = 0; e < m; ++e) {
+        if (col[e] < 0 || col[e] >= n) {
+            set_error("cnd_graph_create: col[%d] = %d out of range", e, col[e]);
+            return CND_EINVAL;
+        }
+        indeg[col[e]]++;
+    }
+    if (ic_prob) {
+        for (int32_t e = 0; e < m; ++e) {
+            const float p = ic_prob[e];
+            if (!(p >= 0.0f && p <= 1.0f)) {
+                set_error("cnd_graph_create: ic_prob[%d] = %g is not in [0, 1]", e, (double)p);
+                return CND_EINVAL;
+            }
+        }
+    }
+    if (lt_weight_fx) {
+        std::vector<uint64_t> insum((size_t)n, 0);
+        for (int32_t e = 0; e < m; ++e) insum[col[e]] += lt_weight_fx[e];
+        for (int32_t v = 0; v < n; ++v)
+            if (insum[v] > 0xFFFFFFFFull) {
+                set_error("cnd_graph_create: LT in-weights of node %d sum to %llu > 2^32-1", v,
+                          (unsigned long long)insum[v]);
+                return CND_EOVERFLOW;
+            }
+    }
+    // ---- in-CSR permutation (counting sort by target, stable in edge id)
+    std::vector<int32_t> in_row_ptr((size_t)n + 1, 0);
+    for (int32_t v = 0; v < n; ++v) in_row_ptr[v + 1] = in_row_ptr[v] + (int32_t)indeg[v];
+    std::vector<int32_t> in_src((size_t)(m > 0 ? m : 1)), in_eid((size_t)(m > 0 ? m : 1));
+    {
+        std::vector<int32_t> cursor(in_row_ptr.begin(), in_row_ptr.end() - 1);
+        for (int32_t u = 0; u < n; ++u)
+            for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+                const int32_t k = cursor[col[e]]++;
+                in_src[k] = u;
+                in_eid[k] = e;
+            }
+    }
+
+    cnd_graph *g = new (std::nothrow) cnd_graph();
+    if (!g) {
+        set_error("cnd_graph_create: host allocation failed");
+        return CND_ENOMEM;
+    }
+    cnd_graph_dev &d = g->d;
+    d.n = n;
+    d.m = m;
+    d.max_out_degree = max_deg;
+    int32_t *d_col = nullptr, *d_tmp_a = nullptr, *d_tmp_b = nullptr;
+    float *d_p = nullptr;
+    uint32_t *d_w = nullptr;
+    cnd_status st = CND_OK;
+    auto fail = [&](cudaError_t e, const char *what) {
+        set_error("cnd_graph_create: %s: %s", what, cudaGetErrorString(e));
+        st = (e == cudaErrorMemoryAllocation) ? CND_ENOMEM : CND_ECUDA;
+    };
+    do {
+        cudaError_t e;
+        if ((e = cudaGetDevice(&d.device)) != cudaSuccess) { fail(e, "cudaGetDevice"); break; }
+        if ((e = cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, d.device)) != cudaSuccess) {
+            fail(e, "attribute");
+            break;
+        }
+        const size_t mb = (size_t)(m > 0 ? m : 1);
+        if ((e = cudaMalloc(&d.row_ptr, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) { fail(e, "alloc row_ptr"); break; }
+        if ((e = cudaMalloc(&d.in_row_ptr, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) { fail(e, "alloc in_row_ptr"); break; }
+        if ((e = cudaMalloc(&d_col, sizeof(int32_t) * mb)) != cudaSuccess) { fail(e, "alloc col"); break; }
+        if ((e = cudaMemcpy(d.row_ptr, row_ptr, sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy row_ptr"); break; }
+        if ((e = cudaMemcpy(d.in_row_ptr, in_row_ptr.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy in_row_ptr"); break; }
+        if (m > 0 && (e = cudaMemcpy(d_col, col, sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy col"); break; }
+        const int threads = 256;
+        const int blocks = (int)std::min<int64_t>(((int64_t)m + threads - 1) / threads + 1, (int64_t)d.num_sms * 8);
+        if (ic_prob) {
+            if ((e = cudaMalloc(&d.ic_edge, sizeof(uint2) * mb)) != cudaSuccess) { fail(e, "alloc ic_edge"); break; }
+            if ((e = cudaMalloc(&d_p, sizeof(float) * mb)) != cudaSuccess) { fail(e, "alloc p"); break; }
+            if (m > 0 && (e = cudaMemcpy(d_p, ic_prob, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy p"); break; }
+            k_build_ic_edges<<<blocks, threads>>>(m, d_col, d_p, d.ic_edge);
+        }
+        if (lt_weight_fx) {
+            if ((e = cudaMalloc(&d.lt_edge, sizeof(uint2) * mb)) != cudaSuccess) { fail(e, "alloc lt_edge"); break; }
+            if ((e = cudaMalloc(&d_w, sizeof(uint32_t) * mb)) != cudaSuccess) { fail(e, "alloc w"); break; }
+            if (m > 0 && (e = cudaMemcpy(d_w, lt_weight_fx, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy w"); break; }
+            k_build_lt_edges<<<blocks, threads>>>(m, d_col, d_w, d.lt_edge);
+        }
+        if ((e = cudaMalloc(&d.in_edge, sizeof(uint4) * mb)) != cudaSuccess) { fail(e, "alloc in_edge"); break; }
+        if ((e = cudaMalloc(&d_tmp_a, sizeof(int32_t) * mb)) != cudaSuccess) { fail(e, "alloc tmp"); break; }
+        if ((e = cudaMalloc(&d_tmp_b, sizeof(int32_t) * mb)) != cudaSuccess) { fail(e, "alloc tmp"); break; }
+        if (m > 0) {
+            if ((e = cudaMemcpy(d_tmp_a, in_src.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy in_src"); break; }
+            if ((e = cudaMemcpy(d_tmp_b, in_eid.data(), sizeof(int32_t) * (size_t)m, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy in_eid"); break; }
+            k_build_in_edges<<<blocks, threads>>>(m, d_tmp_a, d_tmp_b, d.ic_edge, d.lt_edge, d.in_edge);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) { fail(e, "launch"); break; }
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) { fail(e, "sync"); break; }
+    } while (0);
+    cudaFree(d_col);
+    cudaFree(d_p);
+    cudaFree(d_w);
+    cudaFree(d_tmp_a);
+    cudaFree(d_tmp_b);
+    if (st != CND_OK) {
+        free_dev(d);
+        delete g;
+        return st;
+    }
+    *out = g;
+    return CND_OK;
+}
+
+void cnd_graph_destroy(cnd_graph *g) {
+    if (!g) return;
+    int prev = 0;
+    cudaGetDevice(&prev);
+    cudaSetDevice(g->d.device);
+    free_dev(g->d);
+    cudaSetDevice(prev);
+    delete g;
+}
+
+cnd_status cnd_graph_info(const cnd_graph *g, int32_t *n, int32_t *m, int32_t *has_ic, int32_t *has_lt) {
+    clear_error();
+    if (!g) {
+        set_error("cnd_graph_info: graph is NULL");
+        return CND_EINVAL;
+    }
+    if (n) *n = g->d.n;
+    if (m) *m = g->d.m;
+    if (has_ic) *has_ic = g->d.ic_edge != nullptr;
+    if (has_lt) *has_lt = g->d.lt_edge != nullptr;
+    return CND_OK;
+}
+
+cnd_status cnd_philox4x32_10(uint64_t rng_seed, const uint32_t *ctr, int64_t count, uint32_t *out) {
+    clear_error();
+    if (count < 0 || (count > 0 && (!ctr || !out))) {
+        set_error("cnd_philox4x32_10: bad arguments");
+        return CND_EINVAL;
+    }
+    if (count == 0) return CND_OK;
+    uint4 *dc = nullptr, *dout = nullptr;
+    cnd_status st = CND_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaMalloc(&dc, sizeof(uint4) * count)) != cudaSuccess ||
+            (e = cudaMalloc(&dout, sizeof(uint4) * count)) != cudaSuccess ||
+            (e = cudaMemcpy(dc, ctr, sizeof(uint4) * count, cudaMemcpyHostToDevice)) != cudaSuccess) {
+            set_error("cnd_philox4x32_10: %s", cudaGetErrorString(e));
+            st = CND_ECUDA;
+            break;
+        }
+        const int blocks = (int)std::min<int64_t>((count + 255) / 256, 4096);
+        k_philox<<<blocks, 256>>>((uint32_t)rng_seed, (uint32_t)(rng_seed >> 32), dc, count, dout);
+        if ((e = cudaGetLastError()) != cudaSuccess ||
+            (e = cudaMemcpy(out, dout, sizeof(uint4) * count, cudaMemcpyDeviceToHost)) != cudaSuccess) {
+            set_error("cnd_philox4x32_10: %s", cudaGetErrorString(e));
+            st = CND_ECUDA;
+        }
+    } while (0);
+    cudaFree(dc);
+    cudaFree(dout);
+    return st;
+}
+
+}  // extern "C"

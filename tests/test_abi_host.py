@@ -1,0 +1,65 @@
+"""C-ABI library checks that need no GPU: it loads, exports every declared
+symbol, and rejects malformed input on the host before touching the device."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import paper_2404_17059_gb300 as P
+from paper_2404_17059_gb300 import binding, inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "cnd.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(cnd_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = binding.load()
+    decl = declared_symbols()
+    assert "cnd_ic_simulate" in decl and "cnd_graph_create" in decl
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(binding.EXPORTS) == decl
+
+
+def test_opts_struct_layout():
+    import ctypes
+    o = P.cnd_sim_opts_init()
+    assert ctypes.sizeof(o) == 104
+    assert binding.cnd_sim_opts.timeout_s.offset == 64
+
+
+def _graph():
+    return I.erdos_renyi_m(50, 200, graph_seed=2)
+
+
+def test_graph_validation_on_host():
+    g = _graph()
+    p = I.ic_uniform(g, 0.2)
+    cases = []
+    rp = g.row_ptr.copy(); rp[0] = 1; cases.append((rp, g.col, p, None, P.CND_EINVAL))
+    rp = g.row_ptr.copy(); rp[5], rp[6] = rp[6], rp[5] - 1; cases.append((rp, g.col, p, None, P.CND_EINVAL))
+    c = g.col.copy(); c[7] = g.n; cases.append((g.row_ptr, c, p, None, P.CND_EINVAL))
+    c = g.col.copy(); c[7] = -1; cases.append((g.row_ptr, c, p, None, P.CND_EINVAL))
+    for bad in (np.nan, -1e-9, 1.0000001, np.inf):
+        q = p.copy(); q[3] = bad; cases.append((g.row_ptr, g.col, q, None, P.CND_EINVAL))
+    w = np.full(g.m, 0x80000000, dtype=np.uint32)
+    cases.append((g.row_ptr, g.col, None, w, P.CND_EOVERFLOW))
+    for rp, c, q, w_, want in cases:
+        with pytest.raises(P.CndError) as ei:
+            P.cnd_graph_create(g.n, rp, c, q, w_)
+        assert ei.value.status == want, P.cnd_last_error()
+
+
+def test_lt_weights_wc_helper():
+    g = I.barabasi_albert(300, 3, graph_seed=4)
+    assert np.array_equal(P.cnd_lt_weights_wc(g.n, g.col), I.lt_weighted_cascade(g))
+    w = P.cnd_lt_weights_wc(g.n, g.col).astype(np.uint64)
+    assert np.all(np.bincount(g.col, weights=w, minlength=g.n) <= 0xFFFFFFFF)
+    with pytest.raises(P.CndError):
+        P.cnd_lt_weights_wc(g.n, np.array([0, g.n], dtype=np.int32))

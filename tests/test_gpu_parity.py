@@ -1,0 +1,220 @@
+"""GPU engine vs CPU oracle, bit-exact, through the C ABI (libcnd).
+
+Per-trial spreads, per-node activation counts, edge checks and per-step
+activation counts must be identical: a trial is a pure function of
+(graph, seeds, rng_seed, trial id), so any grouping of trials into words or
+passes, any chunking of rows and any traversal order gives the same result.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2404_17059_gb300 as P
+from paper_2404_17059_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+LC = 128
+
+
+def sim(model, G, seeds, T, rng, **kw):
+    f = P.cnd_ic_simulate_ex if model == "ic" else P.cnd_lt_simulate_ex
+    kw.setdefault("edge_checks", True)
+    kw.setdefault("level_counts_len", LC)
+    return f(G, seeds, T, rng, **kw)
+
+
+def ref(model, g, seeds, T, rng, p=None, w=None, **kw):
+    kw.setdefault("level_counts_len", LC)
+    if model == "ic":
+        return oracle.simulate_threads("ic", g, seeds, T, rng, ic_prob=p, **kw)
+    return oracle.simulate_threads("lt", g, seeds, T, rng, lt_weight=w, **kw)
+
+
+def assert_same(a, b, counts=True):
+    assert a.status == (P.CND_ELIMIT if b.status == oracle.LIMIT else P.CND_OK)
+    assert np.array_equal(a.spread, b.spread), np.nonzero(a.spread != b.spread)[0][:10]
+    if counts:
+        assert np.array_equal(a.node_count, b.node_count)
+        assert a.edge_checks == b.edge_checks
+        assert np.array_equal(a.level_counts, b.level_counts)
+
+
+def both(model, g, G, seeds, T, rng, p=None, w=None, oracle_kw=None, **kw):
+    a = sim(model, G, seeds, T, rng, **kw)
+    okw = dict(oracle_kw or {})
+    if "first_trial" in kw:
+        okw["first_trial"] = kw["first_trial"]
+    if "max_levels" in kw:
+        okw["max_levels"] = kw["max_levels"]
+    b = ref(model, g, seeds, T, rng, p=p, w=w, **okw)
+    assert_same(a, b)
+    return a, b
+
+
+# ------------------------------------------------------------------ fixtures
+@pytest.fixture(scope="module")
+def er0():
+    """Directed ER n=1000, m=10,000, p=0.1, 10 uniform seeds (the small IC workload)."""
+    g = I.erdos_renyi_m(1000, 10_000, graph_seed=1)
+    p = I.ic_uniform(g, 0.1)
+    w = I.lt_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, w)
+    return g, G, p, w, I.uniform_seeds(g.n, 10, 1)
+
+
+@pytest.fixture(scope="module")
+def ba():
+    """BA n=100,000, 5 attachments, symmetrised; WC IC (fp32) and WC LT (fixed point); 50 top-degree seeds."""
+    g = I.barabasi_albert(100_000, 5, graph_seed=1)
+    p = I.ic_weighted_cascade(g)
+    w = I.lt_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, w)
+    return g, G, p, w, I.top_degree_seeds(g, 50)
+
+
+@pytest.fixture(scope="module")
+def rmat14():
+    """R-MAT scale 14 (hubs with thousands of out-edges: exercises row chunking)."""
+    g = I.rmat(14, 16 << 14, graph_seed=3)
+    p = I.ic_uniform_random(g, 0.1, graph_seed=3)
+    w = I.lt_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, w)
+    return g, G, p, w, I.top_degree_seeds(g, 20)
+
+
+# ------------------------------------------------------------------ tests
+def test_device_philox_matches_oracle():
+    rng = np.random.default_rng(5)
+    ctr = rng.integers(0, 1 << 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    for s in (0, 1, 0xDEADBEEFCAFEF00D, (1 << 64) - 1):
+        assert np.array_equal(P.cnd_philox4x32_10(s, ctr), oracle.philox(ctr, s))
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_er_small_workload(er0, model):
+    g, G, p, w, seeds = er0
+    both(model, g, G, seeds, 1000, 1, p=p, w=w)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_ba_workload_all_trials(ba, model):
+    g, G, p, w, seeds = ba
+    both(model, g, G, seeds, 10_000, 1, p=p, w=w)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_rmat_hubs(rmat14, model):
+    g, G, p, w, seeds = rmat14
+    both(model, g, G, seeds, 640, 9, p=p, w=w)
+    both(model, g, G, seeds, 130, 9, p=p, w=w, chunk_edges=3)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_word_widths_and_chunks(er0, model):
+    g, G, p, w, seeds = er0
+    b = ref(model, g, seeds, 1000, 4, p=p, w=w)
+    for wb in (64, 128, 192, 256, 576, 1024, 16384):
+        assert_same(sim(model, G, seeds, 1000, 4, word_bits=wb), b)
+    for ch in (1, 5, 32, 4096):
+        assert_same(sim(model, G, seeds, 1000, 4, chunk_edges=ch), b)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_ragged_trial_counts(ba, model):
+    g, G, p, w, seeds = ba
+    for T in (1, 3, 63, 64, 65, 130, 257):
+        both(model, g, G, seeds, T, 2, p=p, w=w)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_first_trial_offsets(er0, model):
+    g, G, p, w, seeds = er0
+    for ft in (64, 6400, (1 << 34) - 128, (1 << 36) + 64):
+        both(model, g, G, seeds, 200, 3, p=p, w=w, first_trial=ft)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_rng_seeds(er0, model):
+    g, G, p, w, seeds = er0
+    for s in (0, 0xFFFFFFFF, 1 << 32, (1 << 63) + 5):
+        both(model, g, G, seeds, 100, s, p=p, w=w)
+
+
+def test_edge_cases_ic_lt():
+    # isolated nodes, zero-out-degree seeds, a self-loop, parallel edges, p = 0 and p = 1 edges
+    src = np.array([0, 0, 0, 1, 2, 2, 3, 5, 5, 6, 7, 7])
+    dst = np.array([1, 1, 2, 3, 2, 4, 5, 6, 7, 8, 8, 0])
+    g = I.csr_from_edges(10, src, dst, sort=False)
+    p = np.array([0.5, 0.5, 1.0, 0.0, 0.7, 1.0, 0.9, 0.3, 0.6, 1.0, 0.2, 0.4], dtype=np.float32)
+    w = I.lt_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, w)
+    for seeds in ([0], [9], [0, 0, 3, 3], [4, 8, 9], list(range(10))):
+        for model in ("ic", "lt"):
+            both(model, g, G, seeds, 300, 5, p=p, w=w)
+    for model in ("ic", "lt"):
+        a = sim(model, G, [], 100, 1)
+        assert np.all(a.spread == 0) and np.all(a.node_count == 0) and a.edge_checks == 0
+        a = sim(model, G, [0], 0, 1)
+        assert a.spread.size == 0 and np.all(a.node_count == 0)
+
+
+def test_no_edges_graph():
+    g = I.Graph(n=5, row_ptr=np.zeros(6, np.int32), col=np.zeros(0, np.int32))
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, np.zeros(0, np.float32), np.zeros(0, np.uint32))
+    for model in ("ic", "lt"):
+        a = sim(model, G, [1, 3], 77, 1)
+        assert np.all(a.spread == 2) and a.edge_checks == 0
+        assert np.array_equal(a.node_count, np.array([0, 77, 0, 77, 0]))
+
+
+def test_p_one_is_reachability(er0):
+    g, _, _, _, seeds = er0
+    p1 = I.ic_uniform(g, 1.0)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p1, None)
+    both("ic", g, G, seeds, 70, 1, p=p1)
+    p0 = I.ic_uniform(g, 0.0)
+    G0 = P.cnd_graph_create(g.n, g.row_ptr, g.col, p0, None)
+    a = sim("ic", G0, seeds, 70, 1)
+    assert np.all(a.spread == len(set(seeds.tolist())))
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_level_cap(ba, model):
+    g, G, p, w, seeds = ba
+    for cap in (1, 3, 10):
+        a, b = both(model, g, G, seeds, 200, 7, p=p, w=w, max_levels=cap)
+        assert a.status == P.CND_ELIMIT
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_device_pointers_match_host(ba, model):
+    torch = pytest.importorskip("torch")
+    g, G, p, w, seeds = ba
+    host = sim(model, G, seeds, 1000, 11)
+    d = sim(model, G, torch.as_tensor(seeds, device="cuda"), 1000, 11)
+    torch.cuda.synchronize()
+    assert np.array_equal(d.spread.cpu().numpy(), host.spread)
+    assert np.array_equal(d.node_count.cpu().numpy(), host.node_count)
+    assert d.edge_checks == host.edge_checks
+    assert np.array_equal(d.level_counts.cpu().numpy(), host.level_counts)
+
+
+def test_bad_device_seed_rejected(er0):
+    torch = pytest.importorskip("torch")
+    g, G, p, w, seeds = er0
+    s = torch.tensor([1, 2, g.n + 5], dtype=torch.int32, device="cuda")
+    with pytest.raises(P.CndError) as ei:
+        sim("ic", G, s, 64, 1)
+    assert ei.value.status == P.CND_EINVAL
+    # the context is still usable
+    both("ic", g, G, seeds, 64, 1, p=p, w=w)
+
+
+def test_plain_entry_points(er0):
+    g, G, p, w, seeds = er0
+    a = P.cnd_ic_simulate(G, seeds, 500, 1)
+    b = ref("ic", g, seeds, 500, 1, p=p)
+    assert np.array_equal(a.spread, b.spread) and np.array_equal(a.node_count, b.node_count)
+    a = P.cnd_lt_simulate(G, seeds, 500, 1)
+    b = ref("lt", g, seeds, 500, 1, w=w)
+    assert np.array_equal(a.spread, b.spread) and np.array_equal(a.node_count, b.node_count)
