@@ -79,6 +79,30 @@ typedef int32_t cnd_status;
 #define CND_DIR_PUSH 1
 #define CND_DIR_PULL 2
 
+/* Optional measurements of one *_ex call (cnd_sim_opts.stats).  The caller
+ * sets `flags`; every other field is written by the call. */
+#define CND_STATS_TIMING 1 /* CUDA-event time the expansion and finalize kernels */
+#define CND_STATS_COUNT 2  /* count the work terms below in the kernels (adds atomics) */
+typedef struct cnd_sim_stats {
+    int32_t flags;             /* in: CND_STATS_* */
+    int32_t passes;            /* passes over the trials */
+    int32_t word_bits;         /* trials held per node per pass */
+    int32_t levels;            /* expansion steps, summed over passes */
+    int64_t launches;          /* kernels launched by the call */
+    int64_t expand_launches;   /* IC push / LT accumulate kernels */
+    double expand_ms;          /* their summed CUDA-event time (CND_STATS_TIMING) */
+    int64_t finalize_launches; /* frontier finalize / LT threshold kernels */
+    double finalize_ms;
+    int64_t frontier_slots;    /* (node, step) frontier entries */
+    int64_t work_items;        /* (node, step, edge chunk) work items */
+    /* CND_STATS_COUNT only: */
+    int64_t edges_scanned;     /* frontier out-edges read by the expansion kernels */
+    int64_t frontier_words;    /* frontier words loaded by the expansion kernels */
+    int64_t word_checks;       /* (edge, word) pairs with frontier bits: target word read */
+    int64_t draws;             /* Philox blocks drawn (IC coins; LT thresholds) */
+    int64_t updates;           /* IC: target words that gained bits; LT: accumulator adds */
+} cnd_sim_stats;
+
 /* Options of the *_ex entry points.  Zero-initialise (cnd_sim_opts_init). */
 typedef struct cnd_sim_opts {
     int64_t first_trial;       /* id of the first trial; a multiple of 64 (default 0) */
@@ -88,8 +112,8 @@ typedef struct cnd_sim_opts {
     int32_t direction;         /* CND_DIR_* */
     int32_t word_bits;         /* trials held per node per pass: 0 = automatic, else a multiple
                                   of 64 up to 16384 */
-    int32_t device_ptrs;       /* 1: seeds and all outputs are device pointers, and the call
-                                  only enqueues work on `stream` */
+    int32_t device_ptrs;       /* 1: seeds and all outputs are device pointers; the work runs
+                                  on `stream`, and the call returns once it is complete */
     void *stream;              /* cudaStream_t to run on; NULL = legacy default stream */
     int64_t *edge_checks_out;  /* NULL or 1 value: edge checks summed over the trials */
     int64_t *level_counts_out; /* NULL or level_counts_len values: [L] = number of
@@ -100,7 +124,8 @@ typedef struct cnd_sim_opts {
     int32_t chunk_edges;       /* edges per push work item (0 = automatic) */
     int32_t reserved0;
     double timeout_s;          /* > 0: give up with CND_ETIMEOUT after this many seconds */
-    int64_t reserved[4];
+    cnd_sim_stats *stats;      /* NULL or host struct filled by the call */
+    int64_t reserved[3];
 } cnd_sim_opts;
 
 void cnd_sim_opts_init(cnd_sim_opts *opts);

@@ -34,6 +34,33 @@ class CndError(RuntimeError):
         self.status = status
 
 
+CND_STATS_TIMING, CND_STATS_COUNT = 1, 2
+
+
+class cnd_sim_stats(C.Structure):
+    _fields_ = [
+        ("flags", C.c_int32),
+        ("passes", C.c_int32),
+        ("word_bits", C.c_int32),
+        ("levels", C.c_int32),
+        ("launches", C.c_int64),
+        ("expand_launches", C.c_int64),
+        ("expand_ms", C.c_double),
+        ("finalize_launches", C.c_int64),
+        ("finalize_ms", C.c_double),
+        ("frontier_slots", C.c_int64),
+        ("work_items", C.c_int64),
+        ("edges_scanned", C.c_int64),
+        ("frontier_words", C.c_int64),
+        ("word_checks", C.c_int64),
+        ("draws", C.c_int64),
+        ("updates", C.c_int64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class cnd_sim_opts(C.Structure):
     _fields_ = [
         ("first_trial", C.c_int64),
@@ -49,7 +76,8 @@ class cnd_sim_opts(C.Structure):
         ("chunk_edges", C.c_int32),
         ("reserved0", C.c_int32),
         ("timeout_s", C.c_double),
-        ("reserved", C.c_int64 * 4),
+        ("stats", C.c_void_p),
+        ("reserved", C.c_int64 * 3),
     ]
 
 
@@ -171,11 +199,12 @@ class SimResult:
     node_count: object = None    # int32 [n]
     edge_checks: int | None = None
     level_counts: object = None  # int64 [level_counts_len]
+    stats: dict | None = None    # cnd_sim_stats fields, when requested
 
 
 def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=True, node_count=True,
               first_trial=0, max_levels=0, direction="auto", word_bits=0, level_counts_len=0,
-              edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None):
+              edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None, stats=0):
     L = load()
     n_trials = int(n_trials)
     dev = _is_torch_cuda(seeds)
@@ -220,9 +249,15 @@ def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=Tru
         o.pull_permille = int(pull_permille)
         o.chunk_edges = int(chunk_edges)
         o.timeout_s = float(timeout_s)
+        stt = None
+        if stats:
+            stt = cnd_sim_stats()
+            stt.flags = int(stats)
+            o.stats = C.cast(C.pointer(stt), C.c_void_p)
         st = getattr(L, fn_name)(g.handle, seeds_p, int(n_seeds), n_trials, C.c_uint64(rng_seed), sp_p, nc_p,
                                  C.byref(o))
     else:
+        stt = None
         if dev:
             raise ValueError(f"{fn_name} takes host arrays; use the _ex form for device tensors")
         st = getattr(L, fn_name)(g.handle, seeds_p, int(n_seeds), n_trials, C.c_uint64(rng_seed), sp_p, nc_p)
@@ -230,7 +265,7 @@ def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=Tru
     ecv = None
     if ec is not None:
         ecv = int(ec[0].item()) if dev else int(ec[0])
-    return SimResult(st, sp, nc, ecv, lc)
+    return SimResult(st, sp, nc, ecv, lc, stt.as_dict() if stt is not None else None)
 
 
 def cnd_ic_simulate(g, seeds, n_trials, rng_seed, *, spread=True, node_count=True) -> SimResult:

@@ -1,29 +1,35 @@
 // Bit-parallel, level-synchronous Monte Carlo engine for the IC and LT models
 // on sm_103a.
 //
-// Layout.  Trials are packed 64 to a uint64 word; a pass ("slab") holds B
-// consecutive words, i.e. 64*B trials, and every node owns B contiguous words
-// of each state array (node-major), so the state of one node in all of the
-// slab's trials is one contiguous run of 8*B bytes:
+// Layout.  Trials are packed 64 to a uint64 word; a pass holds B <= 256
+// consecutive words (64*B trials) and every node owns B contiguous words of
+// each state array (node-major), so the state of one node in all of the pass's
+// trials is one contiguous run of 8*B bytes:
 //   vis[v*B + w]   bit b set <=> node v is active in trial 64*(w0+w) + b
 //   nxt[v*B + w]   IC: bits first activated in the current step
-//                  LT: bits whose accumulator grew in the current step
+//                  LT: trials whose accumulator grew in the current step
+//   dmask[v*nq+q]  bit w%64 of word q set <=> nxt[v*B + w] != 0 (nq = ceil(B/64))
 //   acc[(v*B + w)*64 + b]   LT: active in-weight of v in that trial (uint32)
-// The frontier of a step is a compact list of (node, B frontier words)
-// "slots" plus work items (slot, edge chunk) that split long rows into chunks
-// of `chunk` edges, so that hubs are spread over many warps.
+//
+// Frontier.  In a step, a node is newly active in only some of the pass's
+// trials, and those trials are scattered over its words; the frontier keeps
+// only the words that carry bits: a list of slots (node, pair offset, pair
+// count) over a pool of (word index, frontier bits) pairs.  Work items
+// (slot, edge offset) cover about kTasks (edge, pair) tasks each, and a warp
+// spreads the tasks of an item evenly over its lanes, so hubs are split over
+// many warps and no lane idles on empty words.
 //
 // Steps (Sec. 3 "Algorithms": only out-neighbours of nodes newly active in
 // the previous step are examined, Observation 1):
-//   seed select + finalize  -> step-0 frontier (seeds in every valid trial)
-//   IC:  push       for every frontier edge (u,v) and word: c = f_u & ~vis_v;
-//                   coins are drawn only for the 4-trial groups that have a
-//                   bit in c; live bits are or-ed into vis_v and nxt_v
-//        finalize   nxt -> next frontier slots, nxt cleared
-//   LT:  push       for every frontier edge (u,v) and word: for each trial in
-//                   f_u & ~vis_v add w(u,v) to acc; mark the word touched
-//        finalize   for every touched word, draw the thresholds of the
-//                   touched trials and activate where acc > theta
+//   seeds      every valid word of every distinct seed
+//   IC push    task (edge u->v, pair (w, f)): c = f & ~vis_v[w]; coins are
+//              drawn only for the 4-trial blocks with a bit in c; live bits are
+//              or-ed into vis_v and nxt_v; v is listed once per step
+//   LT push    task: for each trial of f & ~vis_v[w], add w(u,v) to acc and
+//              mark the word touched; v is listed once per step
+//   finalize   per listed node: IC takes the dirty words of nxt; LT draws the
+//              thresholds of the touched trials and activates where
+//              acc > theta; the non-empty words become the next frontier
 // then the per-trial spread and per-node counts are reduced from vis.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -37,42 +43,83 @@
 
 namespace cnd {
 
+constexpr int kMaxB = 256;   // words per node per pass
+constexpr int kTasks = 256;  // (edge, pair) tasks per push work item
+constexpr int kWarps = 8;    // warps per block
+constexpr int kBlock = 32 * kWarps;
+
 struct Frontier {
-    int32_t *node = nullptr;  // [cap] node of each slot
-    uint64_t *bits = nullptr; // [cap * B] frontier words of each slot
-    int2 *work = nullptr;     // [work_cap] (slot, chunk index)
-    int32_t *cnt = nullptr;   // device [2]: slots, work items
+    int32_t *node = nullptr;   // [n] node of each slot
+    int32_t *poff = nullptr;   // [n] first pair of each slot in the pool
+    int32_t *pk = nullptr;     // [n] number of pairs of each slot
+    uint16_t *pw = nullptr;    // [n*B] pool: word index
+    uint64_t *pb = nullptr;    // [n*B] pool: frontier bits
+    int2 *work = nullptr;      // [work_cap] (slot, first edge of the item within the row)
+    int32_t *cnt = nullptr;    // device [4]: slots, work items, pool pairs, listed nodes
 };
 
 struct Params {
-    int32_t n;
-    int32_t B;
-    int32_t chunk;
+    int32_t n, B, nq;
+    int32_t chunk;             // > 0: fixed edges per work item
     const int32_t *row_ptr;
-    const uint2 *edge;        // {col, IC threshold} or {col, LT weight}
-    uint64_t *vis;
-    uint64_t *nxt;
+    const uint2 *edge;         // {col, IC threshold} or {col, LT weight}
+    uint64_t *vis, *nxt, *dmask;
     uint32_t *acc;
-    uint32_t *mark;           // [n] last stamp that enqueued the node
-    Frontier in, out, tmp;
+    uint32_t *mark;            // [n] last stamp that listed the node
+    int32_t *list;             // [n] nodes listed by the current step's push
+    Frontier in, out;          // out.cnt[3] counts `list`
     uint32_t stamp;
-    uint32_t k0, k1;          // Philox key
-    uint64_t g_base;          // trial-group index (trial >> 2) of bit 0 of word 0
+    uint32_t k0, k1;           // Philox key
+    uint64_t g_base;           // trial-block index (trial >> 2) of bit 0 of word 0
     unsigned long long *level_counts;
     int32_t lc_len;
-    int32_t level;            // step whose frontier is being produced
-    const uint64_t *valid;    // [B] valid-trial mask of each word
+    int32_t level;             // step whose frontier is being produced
+    const uint64_t *valid;     // [B] valid-trial mask of each word
+    int32_t nvalid;            // words of this pass that hold trials
+    unsigned long long *ctr;   // null, or [C_N] work counters (CND_STATS_COUNT)
 };
 
+enum { C_EDGES, C_FWORDS, C_WCHECKS, C_DRAWS, C_UPDATES, C_N };
+
 // ---------------------------------------------------------------- helpers
-__device__ __forceinline__ uint64_t ld_cg(const uint64_t *p) { return __ldcg((const unsigned long long *)p); }
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ void count_add(const Params &p, int i, unsigned long long v) {
+    if (!p.ctr) return;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane_id() == 0 && v) atomicAdd(&p.ctr[i], v);
+}
+
+__device__ __forceinline__ void add_level_count(const Params &p, unsigned long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    if (lane_id() == 0 && v && p.level < p.lc_len) atomicAdd(&p.level_counts[p.level], v);
+}
+
+// Edges per work item for a slot with k pairs.
+__device__ __forceinline__ int edges_per_item(const Params &p, int k) {
+    return p.chunk > 0 ? p.chunk : max(1, kTasks / max(k, 1));
+}
+
+// t / k for t < 2^32 / k (k <= kMaxB): multiply by ceil-ish reciprocal.
+__device__ __forceinline__ uint32_t div_by(uint32_t t, uint32_t k, uint32_t magic) {
+    return k == 1 ? t : __umulhi(t, magic);
+}
+
+// Position of the r-th (0-based) set bit of x; x has more than r set bits.
+__device__ __forceinline__ int nth_set_bit(uint64_t x, int r) {
+    const uint32_t lo = (uint32_t)x;
+    const int c = __popc(lo);
+    if (r < c) return (int)__fns(lo, 0, r + 1);
+    return 32 + (int)__fns((uint32_t)(x >> 32), 0, r - c + 1);
+}
 
 // IC: bits of `c` (trials of one word) whose edge e is live.  Coins come in
 // blocks of four trials, one Philox call per block that has a bit in c.
 __device__ __forceinline__ uint64_t ic_live_bits(uint32_t e, uint64_t g0, uint64_t c, uint32_t thr, uint32_t k0,
-                                                 uint32_t k1) {
+                                                 uint32_t k1, uint32_t &draws) {
     uint64_t live = 0;
     while (c) {
+        ++draws;
         const int j = (__ffsll((long long)c) - 1) >> 2;
         const uint64_t g = g0 + (uint64_t)j;
         const U4 r = philox4x32_10(e, (uint32_t)g, 0u, (uint32_t)(g >> 32), k0, k1);
@@ -84,31 +131,37 @@ __device__ __forceinline__ uint64_t ic_live_bits(uint32_t e, uint64_t g0, uint64
     return live;
 }
 
-__device__ __forceinline__ void add_level_count(const Params &p, unsigned long long v) {
-    // one atomic per warp
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    if ((threadIdx.x & 31) == 0 && v && p.level < p.lc_len) atomicAdd(&p.level_counts[p.level], v);
-}
+// Per-warp staging of the nodes a push lists for the finalize kernel: one
+// global atomic per 32 or more nodes instead of one per warp iteration.
+struct ListBuf {
+    int32_t *buf;  // 64 entries in shared memory
+    int n;         // warp-uniform fill level
 
-// Append the work items of the slots held by group leaders (`lead`) of this warp.
-__device__ __forceinline__ void emit_work(const Params &p, bool lead, int slot, int v) {
-    int nch = 0;
-    if (lead) {
-        const int deg = p.row_ptr[v + 1] - p.row_ptr[v];
-        nch = (deg + p.chunk - 1) / p.chunk;
-    }
-    const int lane = threadIdx.x & 31;
-    unsigned pending = __ballot_sync(kFull, nch > 0);
-    while (pending) {
-        const int src = __ffs(pending) - 1;
-        pending &= pending - 1;
-        const int nc = __shfl_sync(kFull, nch, src);
-        const int sl = __shfl_sync(kFull, slot, src);
+    __device__ __forceinline__ void flush(const Params &p) {
+        __syncwarp();
         int base = 0;
-        if (lane == 0) base = atomicAdd(&p.out.cnt[1], nc);
+        if (lane_id() == 0) base = atomicAdd(&p.out.cnt[3], n);
         base = __shfl_sync(kFull, base, 0);
-        for (int c = lane; c < nc; c += 32) p.out.work[base + c] = make_int2(sl, c);
+        for (int j = lane_id(); j < n; j += 32) p.list[base + j] = buf[j];
+        __syncwarp();
+        n = 0;
     }
+
+    // List v once per step (the stamp in mark[v] says whether it already is).
+    __device__ __forceinline__ void add(const Params &p, bool want, int v) {
+        const bool need = want && __ldcg(&p.mark[v]) != p.stamp && atomicExch(&p.mark[v], p.stamp) != p.stamp;
+        const unsigned nm = __ballot_sync(kFull, need);
+        if (nm) {
+            if (need) buf[n + __popc(nm & ((1u << lane_id()) - 1u))] = v;
+            n += __popc(nm);
+            if (n >= 32) flush(p);
+        }
+    }
+};
+
+// Mark word w of v dirty the first time nxt[v][w] gains bits in this step.
+__device__ __forceinline__ void mark_dirty(const Params &p, int v, int w, uint64_t old_nxt) {
+    if (old_nxt == 0) atomicOr((unsigned long long *)(p.dmask + (size_t)v * p.nq + (w >> 6)), 1ull << (w & 63));
 }
 
 // ---------------------------------------------------------------- seeds
@@ -119,252 +172,280 @@ __global__ void k_seed_select(Params p, const int32_t *__restrict__ seeds, int32
             atomicExch(bad, 1);
             continue;
         }
-        if (atomicExch(&p.mark[s], p.stamp) != p.stamp) {
-            const int slot = atomicAdd(&p.out.cnt[0], 1);
-            p.out.node[slot] = s;
-        }
+        if (atomicExch(&p.mark[s], p.stamp) != p.stamp) p.list[atomicAdd(&p.out.cnt[3], 1)] = s;
     }
 }
 
-// Fill the frontier words of the out-list slots.  SEED: from the valid masks
-// (and set vis); IC: from nxt (cleared on the way).  Emits the work items.
-template <int LPE, int NW, bool SEED>
-__global__ void __launch_bounds__(256) k_finalize(Params p) {
-    constexpr int G = 32 / LPE;
-    const int lane = threadIdx.x & 31, sub = lane % LPE, grp = lane / LPE;
-    const int count = p.out.cnt[0];
+// ---------------------------------------------------------------- finalize
+// Word index of the r-th word listed in a node's dirty mask (nq <= 4 words).
+__device__ __forceinline__ int word_at(const uint64_t (&dm)[4], int r) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int c = __popcll(dm[q]);
+        if (r < c) return 64 * q + nth_set_bit(dm[q], r);
+        r -= c;
+    }
+    return 0;
+}
+
+// Warps take the listed nodes 32 at a time (one per lane), size and place
+// their slots, pool pairs and work items with one atomic per counter per 32
+// nodes, then collect each node's words cooperatively.
+//   MODE 0 (seeds): every valid word, vis set to the valid mask.
+//   MODE 1 (IC):    the dirty words of nxt, cleared on the way.
+//   MODE 2 (LT):    threshold test of the touched trials of the dirty words;
+//                   the words with new activations go to the slot.
+template <int MODE>
+__global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
+    const int lane = lane_id();
+    const unsigned below = (1u << lane) - 1u;
+    const int count = p.out.cnt[3];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int B = p.B;
+    const int B = p.B, nq = p.nq;
     unsigned long long pc = 0;
-    for (int base = warp * G; base < count; base += n_warps * G) {
-        const int slot = base + grp;
-        const bool act = slot < count;
-        const int v = act ? p.out.node[slot] : 0;
+    uint32_t n_dr = 0;
+    for (int base = warp * 32; base < count; base += n_warps * 32) {
+        const int i = base + lane;
+        const bool act = i < count;
+        const int v = act ? p.list[i] : 0;
+        uint64_t dm[4] = {0ull, 0ull, 0ull, 0ull};
+        int K = 0;
         if (act) {
+            if (MODE == 0) {
+                K = p.nvalid;
+            } else {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const int w = sub + k * LPE;
-                if (w >= B) break;
-                const size_t idx = (size_t)v * B + w;
-                uint64_t x;
-                if (SEED) {
-                    x = p.valid[w];
-                    p.vis[idx] = x;
-                } else {
-                    x = p.nxt[idx];
-                    p.nxt[idx] = 0;
-                }
-                p.out.bits[(size_t)slot * B + w] = x;
-                pc += __popcll(x);
-            }
-        }
-        emit_work(p, act && sub == 0, slot, v);
-    }
-    add_level_count(p, pc);
-}
-
-// ---------------------------------------------------------------- IC push
-template <int LPE, int NW>
-__global__ void __launch_bounds__(256) k_ic_push(Params p) {
-    constexpr int EPW = 32 / LPE;
-    const int lane = threadIdx.x & 31, sub = lane % LPE, grp = lane / LPE;
-    const unsigned gmask = (LPE == 32) ? kFull : (((1u << LPE) - 1u) << (grp * LPE));
-    const int n_work = p.in.cnt[1];
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int B = p.B;
-    for (int wi = warp; wi < n_work; wi += n_warps) {
-        const int2 it = p.in.work[wi];
-        const int u = p.in.node[it.x];
-        const int e_begin = p.row_ptr[u] + it.y * p.chunk;
-        const int e_end = min(p.row_ptr[u + 1], e_begin + p.chunk);
-        uint64_t f[NW];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const int w = sub + k * LPE;
-            f[k] = (w < B) ? p.in.bits[(size_t)it.x * B + w] : 0ull;
-        }
-        for (int e0 = e_begin; e0 < e_end; e0 += EPW) {
-            const int e = e0 + grp;
-            bool fresh = false;
-            int v = 0;
-            if (e < e_end) {
-                const uint2 ed = __ldg(&p.edge[e]);
-                v = (int)ed.x;
-                const uint32_t thr = ed.y;
-                if (thr != 0u) {
-#pragma unroll
-                    for (int k = 0; k < NW; ++k) {
-                        if (f[k] == 0) continue;
-                        const int w = sub + k * LPE;
-                        uint64_t *vp = p.vis + (size_t)v * B + w;
-                        const uint64_t c = f[k] & ~ld_cg(vp);
-                        if (c == 0) continue;
-                        uint64_t nb = c;
-                        if (thr != kAlways) nb &= ic_live_bits((uint32_t)e, p.g_base + 16ull * w, c, thr, p.k0, p.k1);
-                        if (nb == 0) continue;
-                        nb &= ~(uint64_t)atomicOr((unsigned long long *)vp, (unsigned long long)nb);
-                        if (nb == 0) continue;
-                        atomicOr((unsigned long long *)(p.nxt + (size_t)v * B + w), (unsigned long long)nb);
-                        fresh = true;
+                for (int q = 0; q < 4; ++q)
+                    if (q < nq) {
+                        dm[q] = p.dmask[(size_t)v * nq + q];
+                        p.dmask[(size_t)v * nq + q] = 0ull;
+                        K += __popcll(dm[q]);
                     }
-                }
-            }
-            const unsigned fb = __ballot_sync(kFull, fresh);
-            bool need = (sub == 0) && (fb & gmask);
-            if (need) need = atomicExch(&p.mark[v], p.stamp) != p.stamp;
-            const unsigned nm = __ballot_sync(kFull, need);
-            if (nm) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&p.out.cnt[0], __popc(nm));
-                base = __shfl_sync(kFull, base, 0);
-                if (need) p.out.node[base + __popc(nm & ((1u << lane) - 1u))] = v;
             }
         }
-    }
-}
-
-// ---------------------------------------------------------------- LT push
-// Phase A of an LT step: accumulate the weight of every frontier in-neighbour
-// into the trials where the target is still inactive; list the targets in tmp.
-template <int LPE, int NW>
-__global__ void __launch_bounds__(256) k_lt_push(Params p) {
-    constexpr int EPW = 32 / LPE;
-    const int lane = threadIdx.x & 31, sub = lane % LPE, grp = lane / LPE;
-    const unsigned gmask = (LPE == 32) ? kFull : (((1u << LPE) - 1u) << (grp * LPE));
-    const int n_work = p.in.cnt[1];
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
-    const int B = p.B;
-    for (int wi = warp; wi < n_work; wi += n_warps) {
-        const int2 it = p.in.work[wi];
-        const int u = p.in.node[it.x];
-        const int e_begin = p.row_ptr[u] + it.y * p.chunk;
-        const int e_end = min(p.row_ptr[u + 1], e_begin + p.chunk);
-        uint64_t f[NW];
+        int kept = K;
+        if (MODE == 2) {
+            // threshold test, node by node; the result bits replace the touched
+            // bits in nxt until the copy below
+            kept = 0;
+            for (int s = 0; s < 32; ++s) {
+                const int Ks = __shfl_sync(kFull, K, s);
+                if (Ks == 0) continue;
+                const int vs = __shfl_sync(kFull, v, s);
+                uint64_t dms[4];
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            const int w = sub + k * LPE;
-            f[k] = (w < B) ? p.in.bits[(size_t)it.x * B + w] : 0ull;
-        }
-        for (int e0 = e_begin; e0 < e_end; e0 += EPW) {
-            const int e = e0 + grp;
-            bool touched = false;
-            int v = 0;
-            if (e < e_end) {
-                const uint2 ed = __ldg(&p.edge[e]);
-                v = (int)ed.x;
-                const uint32_t wt = ed.y;
-                if (wt != 0u) {
-#pragma unroll
-                    for (int k = 0; k < NW; ++k) {
-                        if (f[k] == 0) continue;
-                        const int w = sub + k * LPE;
-                        const size_t idx = (size_t)v * B + w;
-                        uint64_t c = f[k] & ~p.vis[idx];
-                        if (c == 0) continue;
-                        uint32_t *a = p.acc + idx * 64;
-                        atomicOr((unsigned long long *)(p.nxt + idx), (unsigned long long)c);
-                        while (c) {
-                            const int b = __ffsll((long long)c) - 1;
-                            c &= c - 1;
-                            atomicAdd(a + b, wt);
+                for (int q = 0; q < 4; ++q) dms[q] = __shfl_sync(kFull, dm[q], s);
+                int kc = 0;
+                for (int r0 = 0; r0 < Ks; r0 += 32) {
+                    const int r = r0 + lane;
+                    uint64_t nb = 0;
+                    if (r < Ks) {
+                        const int w = word_at(dms, r);
+                        const size_t idx = (size_t)vs * B + w;
+                        const uint64_t vis = p.vis[idx];
+                        uint64_t cand = p.nxt[idx] & ~vis;
+                        const uint32_t *a = p.acc + idx * 64;
+                        while (cand) {
+                            ++n_dr;
+                            const int j = (__ffsll((long long)cand) - 1) >> 2;
+                            const uint64_t g = p.g_base + 16ull * w + (uint64_t)j;
+                            const U4 th = philox4x32_10((uint32_t)vs, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.k0, p.k1);
+                            const int b0 = 4 * j;
+                            const uint4 av = *reinterpret_cast<const uint4 *>(a + b0);
+                            uint64_t hit = (uint64_t)(av.x > th.x) | ((uint64_t)(av.y > th.y) << 1) |
+                                           ((uint64_t)(av.z > th.z) << 2) | ((uint64_t)(av.w > th.w) << 3);
+                            nb |= (hit << b0) & cand;
+                            cand &= ~(0xFull << b0);
                         }
-                        touched = true;
+                        if (nb) p.vis[idx] = vis | nb;
+                        p.nxt[idx] = nb;
+                        pc += __popcll(nb);
                     }
+                    kc += __popc(__ballot_sync(kFull, nb != 0ull));
                 }
-            }
-            const unsigned fb = __ballot_sync(kFull, touched);
-            bool need = (sub == 0) && (fb & gmask);
-            if (need) need = atomicExch(&p.mark[v], p.stamp) != p.stamp;
-            const unsigned nm = __ballot_sync(kFull, need);
-            if (nm) {
-                int base = 0;
-                if (lane == 0) base = atomicAdd(&p.tmp.cnt[0], __popc(nm));
-                base = __shfl_sync(kFull, base, 0);
-                if (need) p.tmp.node[base + __popc(nm & ((1u << lane) - 1u))] = v;
+                if (lane == s) kept = kc;
             }
         }
+        // places for the 32 nodes: inclusive warp scans of pairs, slots, items
+        const int has = kept > 0 ? 1 : 0;
+        const int deg = has ? p.row_ptr[v + 1] - p.row_ptr[v] : 0;
+        const int ne = edges_per_item(p, kept);
+        const int nch = deg > 0 ? (deg + ne - 1) / ne : 0;
+        int sk = kept, sh = has, sc = nch;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a1 = __shfl_up_sync(kFull, sk, o), a2 = __shfl_up_sync(kFull, sh, o),
+                      a3 = __shfl_up_sync(kFull, sc, o);
+            if (lane >= o) {
+                sk += a1;
+                sh += a2;
+                sc += a3;
+            }
+        }
+        int pool0 = 0, slot0 = 0, item0 = 0;
+        if (lane == 31) {
+            if (sk) pool0 = atomicAdd(&p.out.cnt[2], sk);
+            if (sh) slot0 = atomicAdd(&p.out.cnt[0], sh);
+            if (sc) item0 = atomicAdd(&p.out.cnt[1], sc);
+        }
+        pool0 = __shfl_sync(kFull, pool0, 31);
+        slot0 = __shfl_sync(kFull, slot0, 31);
+        item0 = __shfl_sync(kFull, item0, 31);
+        const int off = pool0 + sk - kept, slot = slot0 + sh - has, wb = item0 + sc - nch;
+        if (has) {
+            p.out.node[slot] = v;
+            p.out.poff[slot] = off;
+            p.out.pk[slot] = kept;
+        }
+        // copy the words of each node with a slot, and emit its work items
+        unsigned todo = __ballot_sync(kFull, has);
+        while (todo) {
+            const int s = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int Ks = __shfl_sync(kFull, K, s);
+            const int vs = __shfl_sync(kFull, v, s);
+            const int offs = __shfl_sync(kFull, off, s);
+            uint64_t dms[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dms[q] = __shfl_sync(kFull, dm[q], s);
+            int pos = 0;
+            for (int r0 = 0; r0 < Ks; r0 += 32) {
+                const int r = r0 + lane;
+                uint64_t x = 0;
+                int w = 0;
+                if (r < Ks) {
+                    w = MODE == 0 ? r : word_at(dms, r);
+                    const size_t idx = (size_t)vs * B + w;
+                    if (MODE == 0) {
+                        x = p.valid[w];
+                        p.vis[idx] = x;
+                    } else {
+                        x = p.nxt[idx];
+                        p.nxt[idx] = 0ull;
+                    }
+                    if (MODE != 2) pc += __popcll(x);
+                }
+                const unsigned bm = __ballot_sync(kFull, x != 0ull);
+                if (x) {
+                    const int q = pos + __popc(bm & below);
+                    p.out.pw[offs + q] = (uint16_t)w;
+                    p.out.pb[offs + q] = x;
+                }
+                pos += __popc(bm);
+            }
+            const int ncs = __shfl_sync(kFull, nch, s);
+            const int nes = __shfl_sync(kFull, ne, s);
+            const int sls = __shfl_sync(kFull, slot, s);
+            const int wbs = __shfl_sync(kFull, wb, s);
+            for (int c = lane; c < ncs; c += 32) p.out.work[wbs + c] = make_int2(sls, c * nes);
+        }
     }
+    add_level_count(p, pc);
+    count_add(p, C_DRAWS, n_dr);
 }
 
-// Phase B of an LT step: threshold test of every touched (node, trial).
-template <int LPE, int NW>
-__global__ void __launch_bounds__(256) k_lt_finalize(Params p) {
-    constexpr int G = 32 / LPE;
-    const int lane = threadIdx.x & 31, sub = lane % LPE, grp = lane / LPE;
-    const int count = p.tmp.cnt[0];
+// ---------------------------------------------------------------- push
+// One warp per work item: the item's (edge, pair) tasks are spread over the
+// lanes, task t = (edge t / k, pair t % k).
+template <int MODEL>
+__global__ void __launch_bounds__(kBlock) k_push(Params p) {
+    __shared__ uint64_t s_b[kWarps][kMaxB];
+    __shared__ uint16_t s_w[kWarps][kMaxB];
+    __shared__ int32_t s_list[kWarps][64];
+    const int lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    ListBuf lb{s_list[wid], 0};
+    const int n_work = p.in.cnt[1];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int B = p.B;
-    unsigned long long pc = 0;
-    for (int base = warp * G; base < count; base += n_warps * G) {
-        const int ts = base + grp;
-        const bool act = ts < count;
-        const int v = act ? p.tmp.node[ts] : 0;
-        uint64_t nbw[NW];
-        bool any = false;
-#pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            nbw[k] = 0;
-            const int w = sub + k * LPE;
-            if (!act || w >= B) continue;
-            const size_t idx = (size_t)v * B + w;
-            const uint64_t tb = p.nxt[idx];
-            if (tb == 0) continue;
-            p.nxt[idx] = 0;
-            const uint64_t vis = p.vis[idx];
-            uint64_t cand = tb & ~vis;
-            const uint32_t *a = p.acc + idx * 64;
-            uint64_t nb = 0;
-            while (cand) {
-                const int j = (__ffsll((long long)cand) - 1) >> 2;
-                const uint64_t g = p.g_base + 16ull * w + (uint64_t)j;
-                const U4 r = philox4x32_10((uint32_t)v, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.k0, p.k1);
-                const uint32_t th[4] = {r.x, r.y, r.z, r.w};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int b = 4 * j + q;
-                    if ((cand >> b) & 1ull)
-                        if (a[b] > th[q]) nb |= 1ull << b;
+    uint32_t n_edges = 0, n_fw = 0, n_wc = 0, n_dr = 0, n_up = 0;
+    for (int wi = warp; wi < n_work; wi += n_warps) {
+        const int2 it = p.in.work[wi];
+        const int u = p.in.node[it.x];
+        const int off = p.in.poff[it.x];
+        const int k = p.in.pk[it.x];
+        const int row0 = p.row_ptr[u];
+        const int deg = p.row_ptr[u + 1] - row0;
+        const int ne = edges_per_item(p, k);
+        const int e_begin = row0 + it.y;
+        const int e_cnt = min(ne, deg - it.y);
+        for (int j = lane; j < k; j += 32) {
+            s_b[wid][j] = p.in.pb[off + j];
+            s_w[wid][j] = p.in.pw[off + j];
+        }
+        __syncwarp();
+        if (lane == 0) {
+            n_edges += e_cnt;
+            n_fw += k;
+        }
+        const uint32_t T = (uint32_t)e_cnt * (uint32_t)k;
+        const uint32_t magic = 0xFFFFFFFFu / (uint32_t)k + 1u;
+        for (uint32_t t0 = 0; t0 < T; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            bool hit = false;
+            int v = 0;
+            if (t < T) {
+                const uint32_t el = div_by(t, (uint32_t)k, magic);
+                const int j = (int)(t - el * (uint32_t)k);
+                const int e = e_begin + (int)el;
+                const uint2 ed = __ldg(&p.edge[e]);
+                v = (int)ed.x;
+                const int w = s_w[wid][j];
+                const uint64_t f = s_b[wid][j];
+                const size_t idx = (size_t)v * B + w;
+                if (MODEL == 0) {
+                    const uint32_t thr = ed.y;
+                    if (thr != 0u) {
+                        ++n_wc;
+                        const uint64_t c = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
+                        if (c) {
+                            uint64_t nb = c;
+                            if (thr != kAlways)
+                                nb &= ic_live_bits((uint32_t)e, p.g_base + 16ull * w, c, thr, p.k0, p.k1, n_dr);
+                            if (nb) {
+                                nb &= ~(uint64_t)atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)nb);
+                                if (nb) {
+                                    const uint64_t old =
+                                        atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)nb);
+                                    mark_dirty(p, v, w, old);
+                                    ++n_up;
+                                    hit = true;
+                                }
+                            }
+                        }
+                    }
+                } else {
+                    const uint32_t wt = ed.y;
+                    if (wt != 0u) {
+                        ++n_wc;
+                        uint64_t c = f & ~(uint64_t)__ldg((const unsigned long long *)p.vis + idx);
+                        if (c) {
+                            n_up += __popcll(c);
+                            const uint64_t old = atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)c);
+                            mark_dirty(p, v, w, old);
+                            uint32_t *a = p.acc + idx * 64;
+                            while (c) {
+                                const int b = __ffsll((long long)c) - 1;
+                                c &= c - 1;
+                                atomicAdd(a + b, wt);
+                            }
+                            hit = true;
+                        }
+                    }
                 }
-                cand &= ~(0xFull << (4 * j));
             }
-            if (nb) {
-                p.vis[idx] = vis | nb;
-                nbw[k] = nb;
-                any = true;
-                pc += __popcll(nb);
-            }
+            lb.add(p, hit, v);
         }
-        // group-wide "any new bit" -> one slot per activated node
-        const unsigned ab = __ballot_sync(kFull, any);
-        const unsigned gmask = (LPE == 32) ? kFull : (((1u << LPE) - 1u) << (grp * LPE));
-        const bool lead = act && sub == 0 && (ab & gmask);
-        const unsigned lm = __ballot_sync(kFull, lead);
-        int slot = 0;
-        if (lm) {
-            int b0 = 0;
-            if (lane == 0) b0 = atomicAdd(&p.out.cnt[0], __popc(lm));
-            b0 = __shfl_sync(kFull, b0, 0);
-            if (lead) {
-                slot = b0 + __popc(lm & ((1u << lane) - 1u));
-                p.out.node[slot] = v;
-            }
-        }
-        slot = __shfl_sync(kFull, slot, grp * LPE);
-        const bool has = (ab & gmask) && act;
-        if (has) {
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const int w = sub + k * LPE;
-                if (w < B) p.out.bits[(size_t)slot * B + w] = nbw[k];
-            }
-        }
-        emit_work(p, lead, slot, v);
+        __syncwarp();
     }
-    add_level_count(p, pc);
+    if (lb.n) lb.flush(p);
+    count_add(p, C_EDGES, n_edges);
+    count_add(p, C_FWORDS, n_fw);
+    count_add(p, C_WCHECKS, n_wc);
+    count_add(p, C_DRAWS, n_dr);
+    count_add(p, C_UPDATES, n_up);
 }
 
 // ---------------------------------------------------------------- outputs
@@ -396,89 +477,38 @@ __global__ void __launch_bounds__(256) k_spread(const uint64_t *__restrict__ vis
     if (hi) atomicAdd(&spread[w * 64 + 32 + lane], (int)hi);
 }
 
-// Per-node activation counts (accumulated over passes) and edge checks.
-template <int LPE>
+// Per-node activation counts (accumulated over passes) and edge checks; one
+// warp per node, lanes over words.
 __global__ void __launch_bounds__(256) k_counts(const uint64_t *__restrict__ vis, int32_t n, int32_t B,
                                                 const int32_t *__restrict__ row_ptr, int32_t *__restrict__ count,
                                                 unsigned long long *__restrict__ checks) {
-    constexpr int G = 32 / LPE;
-    const int lane = threadIdx.x & 31, sub = lane % LPE, grp = lane / LPE;
+    const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long ck = 0;
-    for (int base = warp * G; base < n; base += n_warps * G) {
-        const int v = base + grp;
+    for (int v = warp; v < n; v += n_warps) {
         int s = 0;
-        if (v < n)
-            for (int w = sub; w < B; w += LPE) s += __popcll(vis[(size_t)v * B + w]);
+        for (int w = lane; w < B; w += 32) s += __popcll(__ldcs((const unsigned long long *)vis + (size_t)v * B + w));
 #pragma unroll
-        for (int o = LPE / 2; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-        if (v < n && sub == 0 && s) {
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
+        if (lane == 0 && s) {
             count[v] += s;
             ck += (unsigned long long)s * (unsigned long long)(row_ptr[v + 1] - row_ptr[v]);
         }
     }
-    for (int o = 16; o > 0; o >>= 1) ck += __shfl_xor_sync(kFull, ck, o);
     if (lane == 0 && ck) atomicAdd(checks, ck);
 }
 
 // ---------------------------------------------------------------- dispatch
-struct Shape {
-    int lpe, nw;
-};
-
-static Shape shape_for(int B) {
-    int lpe = 1;
-    while (lpe < B && lpe < 32) lpe <<= 1;
-    int nw = (B + lpe - 1) / lpe;
-    int r = 1;
-    while (r < nw) r <<= 1;
-    return Shape{lpe, r};
-}
-
-#define CND_SHAPES(X)  \
-    X(1, 1)            \
-    X(2, 1)            \
-    X(4, 1)            \
-    X(8, 1)            \
-    X(16, 1)           \
-    X(32, 1)           \
-    X(32, 2)           \
-    X(32, 4)           \
-    X(32, 8)
-
-enum Kern { K_FIN_SEED, K_FIN_IC, K_IC_PUSH, K_LT_PUSH, K_LT_FIN };
-
-static const void *kernel_ptr(Kern k, Shape s) {
-#define PICK(L, N)                                                  \
-    if (s.lpe == L && s.nw == N) {                                  \
-        switch (k) {                                                \
-            case K_FIN_SEED: return (const void *)k_finalize<L, N, true>;  \
-            case K_FIN_IC: return (const void *)k_finalize<L, N, false>;   \
-            case K_IC_PUSH: return (const void *)k_ic_push<L, N>;          \
-            case K_LT_PUSH: return (const void *)k_lt_push<L, N>;          \
-            case K_LT_FIN: return (const void *)k_lt_finalize<L, N>;       \
-        }                                                           \
-    }
-    CND_SHAPES(PICK)
-#undef PICK
-    return nullptr;
-}
-
-static const void *counts_ptr(int lpe) {
-    switch (lpe) {
-        case 1: return (const void *)k_counts<1>;
-        case 2: return (const void *)k_counts<2>;
-        case 4: return (const void *)k_counts<4>;
-        case 8: return (const void *)k_counts<8>;
-        case 16: return (const void *)k_counts<16>;
-        default: return (const void *)k_counts<32>;
-    }
-}
-
 static cudaError_t launch(const void *fn, int blocks, cudaStream_t st, Params &p) {
     void *args[] = {&p};
-    return cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, 0, st);
+    return cudaLaunchKernel(fn, dim3(blocks), dim3(kBlock), args, 0, st);
+}
+
+static int resident_blocks(const void *fn) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kBlock, 0) != cudaSuccess || b < 1) b = 1;
+    return b;
 }
 
 // ---------------------------------------------------------------- driver
@@ -521,9 +551,8 @@ static void keep_pool(int device) {
     done[device] = true;
 }
 
-static int blocks_for(int items_per_warp_unit, int64_t items, int max_blocks) {
-    const int64_t warps = (items + items_per_warp_unit - 1) / items_per_warp_unit;
-    const int64_t b = (warps + 7) / 8;
+static int blocks_for(int64_t warps, int max_blocks) {
+    const int64_t b = (warps + kWarps - 1) / kWarps;
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, max_blocks));
 }
 
@@ -545,7 +574,7 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         return CND_EINVAL;
     }
     if (n_seeds < 0 || (n_seeds > 0 && !seeds) || n_trials < 0 || n_trials > 0x7FFFFFFFll || o.first_trial < 0 ||
-        (o.first_trial & 63) || o.word_bits < 0 || (o.word_bits & 63) || o.word_bits > 16384 ||
+        (o.first_trial & 63) || o.word_bits < 0 || (o.word_bits & 63) || o.word_bits > 64 * kMaxB ||
         o.level_counts_len < 0 || (o.level_counts_len > 0 && !o.level_counts_out) || o.chunk_edges < 0 ||
         o.direction < 0 || o.direction > 2) {
         set_error("%s: bad arguments (n_seeds, n_trials, first_trial %% 64, word_bits, level_counts, chunk)", fn);
@@ -597,28 +626,67 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
     CND_CUDA_TRY(cudaMemsetAsync(d_checks, 0, sizeof(unsigned long long), st));
     CND_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), st));
 
+    // ---- optional measurements
+    cnd_sim_stats *S = o.stats;
+    if (S) {
+        const int32_t flags = S->flags;
+        memset(S, 0, sizeof(*S));
+        S->flags = flags;
+    }
+    const bool timing = S && (S->flags & CND_STATS_TIMING);
+    unsigned long long *d_ctr = nullptr;
+    if (S && (S->flags & CND_STATS_COUNT)) {
+        CND_CUDA_TRY(W.alloc(&d_ctr, C_N));
+        CND_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * C_N, st));
+    }
+    struct Events {
+        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        ~Events() {
+            for (auto x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    if (timing)
+        for (auto &x : ev.e) CND_CUDA_TRY(cudaEventCreate(&x));
+    bool timing_pending = false;
+    int64_t launches = 0;
+    auto collect_timing = [&]() -> cnd_status {
+        if (!timing_pending) return CND_OK;
+        float a = 0.f, b = 0.f;
+        CND_CUDA_TRY(cudaEventElapsedTime(&a, ev.e[0], ev.e[1]));
+        CND_CUDA_TRY(cudaEventElapsedTime(&b, ev.e[2], ev.e[3]));
+        S->expand_ms += a;
+        S->finalize_ms += b;
+        timing_pending = false;
+        return CND_OK;
+    };
+
     bool limit_hit = false;
     if (total_words > 0) {
         // ---- pass width
         size_t free_b = 0, total_b = 0;
         CND_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         const double budget = 0.6 * (double)free_b;
-        // bytes per word column: vis, nxt, two frontier buffers (+ LT accumulators)
-        const double per_word = (double)n * (4 * 8 + (model == 1 ? 256 : 0));
-        int64_t bmax = o.word_bits ? o.word_bits / 64 : 256;
+        // bytes per word column: vis, nxt, two pair pools (+ LT accumulators)
+        const double per_word = (double)n * (2 * 8 + 2 * 10 + (model == 1 ? 256 : 0));
+        int64_t bmax = o.word_bits ? o.word_bits / 64 : kMaxB;
         bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)(budget / per_word)));
-        bmax = std::min<int64_t>(bmax, 256);
+        bmax = std::min<int64_t>(bmax, kMaxB);
         const int64_t n_pass = (total_words + bmax - 1) / bmax;
         const int B = (int)((total_words + n_pass - 1) / n_pass);
-        const Shape shp = shape_for(B);
-        const int chunk = o.chunk_edges > 0 ? o.chunk_edges : std::max(32, (32 / shp.lpe) * 8);
+        const int nq = (B + 63) / 64;
 
         const size_t nB = (size_t)n * B;
-        const size_t work_cap = (size_t)n + (size_t)G.m / chunk + 1;
+        const size_t work_cap = o.chunk_edges > 0
+                                    ? (size_t)n + (size_t)G.m / std::min(o.chunk_edges, 16384) + 1
+                                    : (size_t)n + 2 * (size_t)G.m * (size_t)B / kTasks + (size_t)G.m + 1;
         Params P{};
         P.n = n;
         P.B = B;
-        P.chunk = chunk;
+        P.nq = nq;
+        // (edge, pair) task indices of an item stay below 2^32 / k for the
+        // reciprocal division in k_push: at most 16384 edges x 256 pairs
+        P.chunk = std::min(o.chunk_edges, 16384);
         P.row_ptr = G.row_ptr;
         P.edge = edge;
         P.k0 = (uint32_t)rng_seed;
@@ -626,28 +694,40 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         P.level_counts = d_lc;
         P.lc_len = lc_len;
         uint64_t *d_valid = nullptr;
-        Frontier fr[3];
+        Frontier fr[2];
         CND_CUDA_TRY(W.alloc(&P.vis, nB));
         CND_CUDA_TRY(W.alloc(&P.nxt, nB));
+        CND_CUDA_TRY(W.alloc(&P.dmask, (size_t)n * nq));
         CND_CUDA_TRY(W.alloc(&P.mark, (size_t)n));
+        CND_CUDA_TRY(W.alloc(&P.list, (size_t)n));
         CND_CUDA_TRY(W.alloc(&d_valid, (size_t)B));
         if (model == 1) CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
-        for (int i = 0; i < 3; ++i) {
-            if (i == 2 && model == 0) break;
+        for (int i = 0; i < 2; ++i) {
             CND_CUDA_TRY(W.alloc(&fr[i].node, (size_t)n));
-            CND_CUDA_TRY(W.alloc(&fr[i].cnt, 2));
-            if (i < 2) {
-                CND_CUDA_TRY(W.alloc(&fr[i].bits, nB));
-                CND_CUDA_TRY(W.alloc(&fr[i].work, work_cap));
-            }
+            CND_CUDA_TRY(W.alloc(&fr[i].poff, (size_t)n));
+            CND_CUDA_TRY(W.alloc(&fr[i].pk, (size_t)n));
+            CND_CUDA_TRY(W.alloc(&fr[i].pw, nB));
+            CND_CUDA_TRY(W.alloc(&fr[i].pb, nB));
+            CND_CUDA_TRY(W.alloc(&fr[i].work, work_cap));
+            CND_CUDA_TRY(W.alloc(&fr[i].cnt, 4));
         }
         P.valid = d_valid;
+        P.ctr = d_ctr;
+        if (S) {
+            S->passes = (int32_t)n_pass;
+            S->word_bits = 64 * B;
+        }
         CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
         CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
+        CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
         if (!t_pinned.h) CND_CUDA_TRY(cudaMallocHost(&t_pinned.h, 4 * sizeof(int32_t)));
         int32_t *hcnt = t_pinned.h;
 
-        const int max_blocks = G.num_sms * 8;
+        const void *k_push_fn = model == 0 ? (const void *)k_push<0> : (const void *)k_push<1>;
+        const void *k_fin_fn = model == 0 ? (const void *)k_finalize<1> : (const void *)k_finalize<2>;
+        const int push_blocks = G.num_sms * resident_blocks(k_push_fn);
+        const int fin_blocks = G.num_sms * resident_blocks(k_fin_fn);
+        const int seed_blocks = G.num_sms * resident_blocks((const void *)k_finalize<0>);
         uint32_t stamp = 0;
         std::vector<uint64_t> valid((size_t)B);
         const auto t0 = std::chrono::steady_clock::now();
@@ -663,6 +743,7 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
                     valid[w] = left >= 64 ? ~0ull : ((1ull << left) - 1ull);
                 }
             }
+            P.nvalid = (int32_t)nw_here;
             CND_CUDA_TRY(cudaMemcpyAsync(d_valid, valid.data(), sizeof(uint64_t) * B, cudaMemcpyHostToDevice, st));
             CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
             if (model == 1) CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
@@ -670,20 +751,29 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
 
             // step 0: seeds
             int cur = 0;
-            CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 2 * sizeof(int32_t), st));
+            CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 4 * sizeof(int32_t), st));
             P.out = fr[cur];
             P.stamp = stamp++;
             P.level = 0;
             if (n_seeds > 0) {
-                k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, max_blocks)), 256, 0, st>>>(P, d_seeds,
-                                                                                                    n_seeds, d_bad);
+                k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, G.num_sms * 8)), 256, 0, st>>>(
+                    P, d_seeds, n_seeds, d_bad);
                 CND_CUDA_TRY(cudaGetLastError());
-                CND_CUDA_TRY(launch(kernel_ptr(K_FIN_SEED, shp), blocks_for(32 / shp.lpe, n_seeds, max_blocks), st, P));
+                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for(n_seeds, seed_blocks), st, P));
+                launches += 2;
             }
             for (int L = 0;; ++L) {
-                CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
                 CND_CUDA_TRY(cudaStreamSynchronize(st));
+                if (timing) {
+                    const cnd_status ts = collect_timing();
+                    if (ts != CND_OK) return ts;
+                }
                 const int32_t slots = hcnt[0], items = hcnt[1];
+                if (S) {
+                    S->frontier_slots += slots;
+                    S->work_items += items;
+                }
                 if (slots == 0) break;
                 if (o.max_levels > 0 && L >= o.max_levels) {
                     limit_hit = true;
@@ -699,23 +789,30 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
                         return CND_ETIMEOUT;
                     }
                 }
-                const int nxt = cur ^ 1;
-                CND_CUDA_TRY(cudaMemsetAsync(fr[nxt].cnt, 0, 2 * sizeof(int32_t), st));
+                const int nx = cur ^ 1;
+                CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
                 P.in = fr[cur];
-                P.out = fr[nxt];
+                P.out = fr[nx];
                 P.stamp = stamp++;
                 P.level = L + 1;
-                const int pb = blocks_for(1, items, max_blocks);
-                if (model == 0) {
-                    CND_CUDA_TRY(launch(kernel_ptr(K_IC_PUSH, shp), pb, st, P));
-                    CND_CUDA_TRY(launch(kernel_ptr(K_FIN_IC, shp), max_blocks, st, P));
-                } else {
-                    CND_CUDA_TRY(cudaMemsetAsync(fr[2].cnt, 0, 2 * sizeof(int32_t), st));
-                    P.tmp = fr[2];
-                    CND_CUDA_TRY(launch(kernel_ptr(K_LT_PUSH, shp), pb, st, P));
-                    CND_CUDA_TRY(launch(kernel_ptr(K_LT_FIN, shp), max_blocks, st, P));
+                if (timing) CND_CUDA_TRY(cudaEventRecord(ev.e[0], st));
+                CND_CUDA_TRY(launch(k_push_fn, blocks_for(items, push_blocks), st, P));
+                if (timing) {
+                    CND_CUDA_TRY(cudaEventRecord(ev.e[1], st));
+                    CND_CUDA_TRY(cudaEventRecord(ev.e[2], st));
                 }
-                cur = nxt;
+                CND_CUDA_TRY(launch(k_fin_fn, fin_blocks, st, P));
+                if (timing) {
+                    CND_CUDA_TRY(cudaEventRecord(ev.e[3], st));
+                    timing_pending = true;
+                }
+                launches += 2;
+                if (S) {
+                    S->levels += 1;
+                    S->expand_launches += 1;
+                    S->finalize_launches += 1;
+                }
+                cur = nx;
             }
             // outputs of this pass
             {
@@ -723,9 +820,9 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
                 dim3 grid((unsigned)((nw_here + 7) / 8), (unsigned)((n + npb - 1) / npb));
                 k_spread<<<grid, 256, 0, st>>>(P.vis, n, B, (int)nw_here, npb, d_spread + w0 * 64);
                 CND_CUDA_TRY(cudaGetLastError());
-                void *args[] = {&P.vis, (void *)&n, (void *)&B, (void *)&G.row_ptr, &d_count, &d_checks};
-                const int cb = blocks_for(32 / shp.lpe, n, max_blocks);
-                CND_CUDA_TRY(cudaLaunchKernel(counts_ptr(shp.lpe), dim3(cb), dim3(256), args, 0, st));
+                k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, st>>>(P.vis, n, B, G.row_ptr, d_count, d_checks);
+                CND_CUDA_TRY(cudaGetLastError());
+                launches += 2;
             }
         }
     }
@@ -750,7 +847,21 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         if (lc_len)
             CND_CUDA_TRY(cudaMemcpyAsync(hlc.data(), d_lc, sizeof(unsigned long long) * lc_len, cudaMemcpyDeviceToHost, st));
     }
+    unsigned long long hctr[C_N] = {0, 0, 0, 0, 0};
+    if (d_ctr) CND_CUDA_TRY(cudaMemcpyAsync(hctr, d_ctr, sizeof(hctr), cudaMemcpyDeviceToHost, st));
     CND_CUDA_TRY(cudaStreamSynchronize(st));
+    if (timing) {
+        const cnd_status ts = collect_timing();
+        if (ts != CND_OK) return ts;
+    }
+    if (S) {
+        S->launches = launches;
+        S->edges_scanned = (int64_t)hctr[C_EDGES];
+        S->frontier_words = (int64_t)hctr[C_FWORDS];
+        S->word_checks = (int64_t)hctr[C_WCHECKS];
+        S->draws = (int64_t)hctr[C_DRAWS];
+        S->updates = (int64_t)hctr[C_UPDATES];
+    }
     if (!dev) {
         if (o.edge_checks_out) *o.edge_checks_out = (int64_t)hchecks;
         for (int i = 0; i < lc_len; ++i) o.level_counts_out[i] = (int64_t)hlc[i];
