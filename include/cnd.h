@@ -192,6 +192,36 @@ cnd_status cnd_lt_weights_wc(int32_t n, int32_t m, const int32_t *col, uint32_t 
  */
 cnd_status cnd_philox4x32_10(uint64_t rng_seed, const uint32_t *ctr, int64_t count, uint32_t *out);
 
+/*
+ * Allocation-free IC simulation.  The paper has no counterpart: this entry
+ * point exists for callers that must not allocate device memory while a
+ * simulation runs -- for example code that runs on a device whose memory is
+ * entirely reserved by another allocator (a framework's caching pool), or a
+ * latency-critical loop that must not wait on the CUDA allocator.  It
+ * computes exactly what cnd_ic_simulate computes, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Its working state lives in one file-scope device array of
+ * CND_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads this library
+ * reserves until the process exits.  Graphs whose state does not fit even
+ * with 64 trials per pass are rejected with CND_EINVAL and a message giving
+ * the bytes needed.  The caller passes inputs and outputs:
+ *   seeds:          device pointer, n_seeds ids (duplicates count once)
+ *   spread_out:     device pointer, n_trials int32 (required if n_trials > 0)
+ *   node_count_out: device pointer, n int32 (required)
+ *   stream:         cudaStream_t the work runs on (NULL = legacy default stream)
+ * The graph must live on the current device.  The call returns when the
+ * results are complete.  The first call on a device looks up the array's
+ * device address (once per device); make that first call before any stream
+ * capture.  Every call shares the array, which keeps the last call's
+ * contents (the call clears what must start at zero): calls that overlap on
+ * the GPU -- from several host threads or on several streams -- race and
+ * must be serialised by the caller.
+ */
+#define CND_NOALLOC_SCRATCH_BYTES (64u << 20)
+cnd_status cnd_ic_simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                                   uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out, void *stream);
+
 /* Message describing the last failure on this host thread ("" if none). */
 const char *cnd_last_error(void);
 

@@ -24,7 +24,7 @@ _DIRS = {"auto": CND_DIR_AUTO, "push": CND_DIR_PUSH, "pull": CND_DIR_PULL}
 EXPORTS = (
     "cnd_sim_opts_init", "cnd_graph_create", "cnd_graph_destroy", "cnd_graph_info", "cnd_ic_simulate",
     "cnd_lt_simulate", "cnd_ic_simulate_ex", "cnd_lt_simulate_ex", "cnd_lt_weights_wc",
-    "cnd_philox4x32_10", "cnd_last_error",
+    "cnd_philox4x32_10", "cnd_last_error", "cnd_ic_simulate_noalloc",
 )
 
 
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = True):
         L.cnd_lt_weights_wc.restype = i32
         L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
         L.cnd_philox4x32_10.restype = i32
+        L.cnd_ic_simulate_noalloc.argtypes = [vp, vp, i32, i64, u64, vp, vp, vp]
+        L.cnd_ic_simulate_noalloc.restype = i32
         L.cnd_last_error.argtypes = []
         L.cnd_last_error.restype = C.c_char_p
         _lib = L
@@ -296,3 +298,23 @@ def cnd_philox4x32_10(rng_seed, ctr) -> np.ndarray:
     out = np.empty_like(ctr)
     _check(load().cnd_philox4x32_10(C.c_uint64(rng_seed), _np_ptr(ctr), int(ctr.shape[0]), _np_ptr(out)))
     return out
+
+
+def cnd_ic_simulate_noalloc(g, seeds, n_trials, rng_seed, spread_out, node_count_out, stream=None) -> int:
+    """IC simulation that allocates nothing: its working state is the library's
+    fixed static device scratch (CND_NOALLOC_SCRATCH_BYTES).  For callers that
+    cannot allocate device memory during the call.  `seeds`, `spread_out`
+    (n_trials int32) and `node_count_out` (n int32) are CUDA tensors the caller
+    owns; calls that overlap on the GPU race on the shared scratch."""
+    import torch
+    for name, t in (("seeds", seeds), ("spread_out", spread_out), ("node_count_out", node_count_out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+            raise TypeError(f"{name} must be a contiguous int32 CUDA tensor")
+    if spread_out.numel() < int(n_trials) or node_count_out.numel() < g.n:
+        raise ValueError("output tensors are too small")
+    strm = stream if stream is not None else torch.cuda.current_stream(seeds.device).cuda_stream
+    st = load().cnd_ic_simulate_noalloc(
+        g.handle, C.c_void_p(seeds.data_ptr()) if seeds.numel() else None, int(seeds.numel()), int(n_trials),
+        C.c_uint64(rng_seed), C.c_void_p(spread_out.data_ptr()) if int(n_trials) else None,
+        C.c_void_p(node_count_out.data_ptr()), strm)
+    return _check(st)

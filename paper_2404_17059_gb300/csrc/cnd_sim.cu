@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <mutex>
 #include <vector>
 
 #include "cnd_common.cuh"
@@ -906,3 +907,227 @@ cnd_status cnd_lt_simulate_ex(const cnd_graph *g, const int32_t *seeds, int32_t 
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Allocation-free IC simulation (cnd_ic_simulate_noalloc).
+//
+// For callers that must not allocate device memory during a simulation call:
+// the working state lives in one file-scope device array of fixed size,
+// reserved when the library is loaded.  The kernels are the ones above; only
+// the placement of their working arrays differs.
+// ============================================================================
+namespace cnd {
+
+constexpr size_t kStaticScratchBytes = (size_t)CND_NOALLOC_SCRATCH_BYTES;
+
+// Scratch shared by every cnd_ic_simulate_noalloc call on this device.  In
+// host code this name is a host-side stand-in; kernels get the device
+// address from cudaGetSymbolAddress (see static_scratch_ptr).
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+static std::mutex g_static_mu;
+static unsigned char *g_static_ptr[64] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (the first call on a device does this; that call should come before
+// any stream capture).
+static cnd_status static_scratch_ptr(int device, unsigned char **out) {
+    if (device < 0 || device >= 64) {
+        set_error("cnd_ic_simulate_noalloc: device %d out of range", device);
+        return CND_EINVAL;
+    }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[device]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_error("cnd_ic_simulate_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return CND_ECUDA;
+        }
+        g_static_ptr[device] = (unsigned char *)ptr;
+    }
+    *out = g_static_ptr[device];
+    return CND_OK;
+}
+
+// Bump placement of the working arrays inside the static scratch.
+struct Arena {
+    unsigned char *base;
+    size_t cap, used;
+    template <class T>
+    T *take(size_t count) {
+        const size_t bytes = ((std::max<size_t>(count, 1) * sizeof(T)) + 255) & ~(size_t)255;
+        T *p = (used + bytes <= cap) ? (T *)(base + used) : nullptr;
+        used += bytes;
+        return p;
+    }
+};
+
+// Working arrays for a pass of B words: fills P and fr when `a.base` is set,
+// and returns the bytes they need either way.
+static size_t place_static(Arena &a, Params &P, Frontier (&fr)[2], int32_t n, int32_t m, int B,
+                           uint64_t **d_valid, unsigned long long **d_checks, int32_t **d_bad) {
+    const int nq = (B + 63) / 64;
+    const size_t nB = (size_t)n * B;
+    const size_t work_cap = (size_t)n + 2 * (size_t)m * (size_t)B / kTasks + (size_t)m + 1;
+    P.vis = a.take<uint64_t>(nB);
+    P.nxt = a.take<uint64_t>(nB);
+    P.dmask = a.take<uint64_t>((size_t)n * nq);
+    P.mark = a.take<uint32_t>((size_t)n);
+    P.list = a.take<int32_t>((size_t)n);
+    *d_valid = a.take<uint64_t>((size_t)B);
+    *d_checks = a.take<unsigned long long>(1);
+    *d_bad = a.take<int32_t>(1);
+    for (int i = 0; i < 2; ++i) {
+        fr[i].node = a.take<int32_t>((size_t)n);
+        fr[i].poff = a.take<int32_t>((size_t)n);
+        fr[i].pk = a.take<int32_t>((size_t)n);
+        fr[i].pw = a.take<uint16_t>(nB);
+        fr[i].pb = a.take<uint64_t>(nB);
+        fr[i].work = a.take<int2>(work_cap);
+        fr[i].cnt = a.take<int32_t>(4);
+    }
+    return a.used;
+}
+
+static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                                   uint64_t rng_seed, int32_t *spread_out, int32_t *count_out, void *stream) {
+    clear_error();
+    const char *fn = "cnd_ic_simulate_noalloc";
+    if (!g) {
+        set_error("%s: graph is NULL", fn);
+        return CND_EINVAL;
+    }
+    const cnd_graph_dev &G = g->d;
+    if (!G.ic_edge && G.m > 0) {
+        set_error("%s: graph was created without IC probabilities", fn);
+        return CND_EINVAL;
+    }
+    if (n_seeds < 0 || (n_seeds > 0 && !seeds) || n_trials < 0 || n_trials > 0x7FFFFFFFll ||
+        (n_trials > 0 && !spread_out) || !count_out) {
+        set_error("%s: bad arguments (seeds, n_trials, spread_out and node_count_out are required)", fn);
+        return CND_EINVAL;
+    }
+    int cur_dev = 0;
+    CND_CUDA_TRY(cudaGetDevice(&cur_dev));
+    if (cur_dev != G.device) {
+        set_error("%s: the graph lives on device %d but device %d is current", fn, G.device, cur_dev);
+        return CND_EINVAL;
+    }
+    const int32_t n = G.n;
+    const int64_t total_words = (n_trials + 63) / 64;
+    // the widest pass that fits the scratch
+    Params P{};
+    Frontier fr[2];
+    uint64_t *d_valid = nullptr;
+    unsigned long long *d_checks = nullptr;
+    int32_t *d_bad = nullptr;
+    int B = (int)std::min<int64_t>(std::max<int64_t>(total_words, 1), kMaxB);
+    for (;; --B) {
+        Arena probe{nullptr, kStaticScratchBytes, 0};
+        if (place_static(probe, P, fr, n, G.m, B, &d_valid, &d_checks, &d_bad) <= kStaticScratchBytes) break;
+        if (B == 1) {
+            set_error("%s: a graph with n = %d, m = %d needs %zu bytes of scratch; the static scratch holds %zu",
+                      fn, n, G.m, place_static(probe, P, fr, n, G.m, 1, &d_valid, &d_checks, &d_bad),
+                      kStaticScratchBytes);
+            return CND_EINVAL;
+        }
+    }
+    unsigned char *base = nullptr;
+    const cnd_status sst = static_scratch_ptr(G.device, &base);
+    if (sst != CND_OK) return sst;
+    Arena arena{base, kStaticScratchBytes, 0};
+    place_static(arena, P, fr, n, G.m, B, &d_valid, &d_checks, &d_bad);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    // the scratch keeps the previous call's contents: clear what must start at zero
+    CND_CUDA_TRY(cudaMemsetAsync(spread_out, 0, sizeof(int32_t) * (size_t)n_trials, st));
+    CND_CUDA_TRY(cudaMemsetAsync(count_out, 0, sizeof(int32_t) * (size_t)n, st));
+    CND_CUDA_TRY(cudaMemsetAsync(d_checks, 0, sizeof(unsigned long long), st));
+    CND_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), st));
+    if (total_words > 0) {
+        const int nq = (B + 63) / 64;
+        const size_t nB = (size_t)n * B;
+        const int64_t n_pass = (total_words + B - 1) / B;
+        P.n = n;
+        P.B = B;
+        P.nq = nq;
+        P.chunk = 0;
+        P.row_ptr = G.row_ptr;
+        P.edge = G.ic_edge;
+        P.k0 = (uint32_t)rng_seed;
+        P.k1 = (uint32_t)(rng_seed >> 32);
+        P.level_counts = nullptr;
+        P.lc_len = 0;
+        P.valid = d_valid;
+        P.ctr = nullptr;
+        CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
+        CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
+        CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
+        const int push_blocks = G.num_sms * resident_blocks((const void *)k_push<0>);
+        const int fin_blocks = G.num_sms * resident_blocks((const void *)k_finalize<1>);
+        const int seed_blocks = G.num_sms * resident_blocks((const void *)k_finalize<0>);
+        uint64_t valid[kMaxB];
+        int32_t hcnt[4];
+        uint32_t stamp = 0;
+        for (int64_t pass = 0; pass < n_pass; ++pass) {
+            const int64_t w0 = pass * B;
+            const int64_t nw_here = std::min<int64_t>(B, total_words - w0);
+            for (int w = 0; w < B; ++w) {
+                const int64_t left = n_trials - (w0 + w) * 64;
+                valid[w] = w >= nw_here ? 0ull : (left >= 64 ? ~0ull : ((1ull << left) - 1ull));
+            }
+            P.nvalid = (int32_t)nw_here;
+            CND_CUDA_TRY(cudaMemcpyAsync(d_valid, valid, sizeof(uint64_t) * B, cudaMemcpyHostToDevice, st));
+            CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
+            P.g_base = (uint64_t)(64 * w0) >> 2;
+            int cur = 0;
+            CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 4 * sizeof(int32_t), st));
+            P.out = fr[cur];
+            P.stamp = stamp++;
+            P.level = 0;
+            if (n_seeds > 0) {
+                k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, G.num_sms * 8)), 256, 0, st>>>(
+                    P, seeds, n_seeds, d_bad);
+                CND_CUDA_TRY(cudaGetLastError());
+                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for(n_seeds, seed_blocks), st, P));
+            }
+            for (;;) {
+                CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CND_CUDA_TRY(cudaStreamSynchronize(st));
+                if (hcnt[0] == 0 || hcnt[1] == 0) break;
+                const int nx = cur ^ 1;
+                CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
+                P.in = fr[cur];
+                P.out = fr[nx];
+                P.stamp = stamp++;
+                P.level += 1;
+                CND_CUDA_TRY(launch((const void *)k_push<0>, blocks_for(hcnt[1], push_blocks), st, P));
+                CND_CUDA_TRY(launch((const void *)k_finalize<1>, fin_blocks, st, P));
+                cur = nx;
+            }
+            const int npb = 4096;
+            dim3 grid((unsigned)((nw_here + 7) / 8), (unsigned)((n + npb - 1) / npb));
+            k_spread<<<grid, 256, 0, st>>>(P.vis, n, B, (int)nw_here, npb, spread_out + w0 * 64);
+            CND_CUDA_TRY(cudaGetLastError());
+            k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, st>>>(P.vis, n, B, G.row_ptr, count_out, d_checks);
+            CND_CUDA_TRY(cudaGetLastError());
+        }
+    }
+    int32_t hbad = 0;
+    CND_CUDA_TRY(cudaMemcpyAsync(&hbad, d_bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CND_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hbad) {
+        set_error("%s: a seed id is out of range", fn);
+        return CND_EINVAL;
+    }
+    return CND_OK;
+}
+
+}  // namespace cnd
+
+extern "C" cnd_status cnd_ic_simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int32_t n_seeds,
+                                              int64_t n_trials, uint64_t rng_seed, int32_t *spread_out,
+                                              int32_t *node_count_out, void *stream) {
+    return cnd::simulate_noalloc(g, seeds, n_seeds, n_trials, rng_seed, spread_out, node_count_out, stream);
+}
