@@ -93,8 +93,14 @@ def source_hash() -> str:
     return h.hexdigest()[:12]
 
 
-def ncu_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on these sources."""
+def ncu_traffic(kernel: str, workload: str, word_checks_per_launch: float):
+    """DRAM bytes per launch, from the committed ncu summary's bytes per word check.
+
+    The summary is taken on a trial sample of the same workload (ncu replays
+    each launch, so the sample keeps the device memory it saves small) and is
+    scaled by the word checks a launch of this run performs.  None unless it
+    was taken on the current sources.
+    """
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -106,7 +112,7 @@ def ncu_traffic(kernel: str, workload: str):
                 continue
             rec = json.loads(line)
             if rec.get("kernel") == kernel and rec.get("workload") == workload and rec.get("src") == cur:
-                return rec.get("dram_bytes_per_launch")
+                return rec["dram_bytes_per_word_check"] * word_checks_per_launch
     return None
 
 
@@ -236,8 +242,20 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     wl = make_workload(args.workload)
+    if args.trials:
+        wl["trials"] = args.trials
     g, T = wl["g"], wl["trials"]
     G = P.cnd_graph_create(g.n, g.row_ptr, g.col, wl["p"], wl["w"])
+    if args.profile_calls:
+        # one IC and one LT call with kernel-counted work (for ncu captures of those launches)
+        seeds_d = torch.as_tensor(wl["seeds"], device=dev)
+        out = {}
+        for model, f in (("ic", P.cnd_ic_simulate_ex), ("lt", P.cnd_lt_simulate_ex)):
+            r = f(G, seeds_d, T, wl["rng_seed"], edge_checks=True, stats=CND_STATS_COUNT)
+            out[model] = r.stats
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_calls": out, "workload": wl["name"], "trials": T, "src": source_hash()}))
+        return 0
     seeds_d = torch.as_tensor(wl["seeds"], device=dev)
     first = rank * (((T + 63) // 64) * 64)  # each rank its own trial range
     stream = torch.cuda.current_stream(dev)
@@ -325,7 +343,7 @@ def run_ours(args):
         n_l = max(1, cs["expand_launches"])
         bpl = alg_bytes(model, cs) / n_l
         avg_ms = exp_ms[model] / max(1, exp_n[model])
-        kern[model] = {"kernel": "k_ic_push" if model == "ic" else "k_lt_push", "launches_per_step": n_l,
+        kern[model] = {"kernel": "k_push<0>" if model == "ic" else "k_push<1>", "launches_per_step": n_l,
                        "avg_launch_ms": avg_ms, "alg_bytes_per_launch": bpl,
                        "achieved_gbs": bpl / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None,
                        "expand_ms_per_step": exp_ms[model] / args.steps,
@@ -335,8 +353,9 @@ def run_ours(args):
     dom = max(kern, key=lambda k: kern[k]["expand_ms_per_step"])
     K = kern[dom]
     ach = K["achieved_gbs"] or 0.0
+    wc_per_launch = K["counts"]["word_checks"] / max(1, K["launches_per_step"])
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": ncu_traffic(K["kernel"], wl["name"]), "kernel": K["kernel"],
+            "traffic": ncu_traffic(K["kernel"], wl["name"], wc_per_launch), "kernel": K["kernel"],
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
 
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl, rank)
@@ -372,6 +391,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ba100k", choices=["ba100k", "er1k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trials", type=int, default=0, help="override the workload's trials per model")
+    ap.add_argument("--profile-calls", action="store_true",
+                    help="run one counted IC and one counted LT call only (for ncu captures)")
     ap.add_argument("--ref-trials", type=int, nargs=2, default=(384, 256),
                     help="IC and LT trials per reference step")
     args = ap.parse_args()

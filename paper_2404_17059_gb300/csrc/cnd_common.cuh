@@ -42,6 +42,40 @@ __host__ __device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, u
     return U4{c0, c1, c2, c3};
 }
 
+// The ten round keys of one Philox key, precomputed once per call so that
+// kernels take them as launch parameters instead of re-deriving them.
+struct RoundKeys {
+    uint32_t k[20];  // round r uses (k[2r], k[2r+1])
+};
+
+inline RoundKeys round_keys(uint64_t key) {
+    RoundKeys rk;
+    uint32_t k0 = (uint32_t)key, k1 = (uint32_t)(key >> 32);
+    for (int r = 0; r < 10; ++r) {
+        rk.k[2 * r] = k0;
+        rk.k[2 * r + 1] = k1;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return rk;
+}
+
+__device__ __forceinline__ U4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                            const RoundKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t a = (uint64_t)0xD2511F53u * c0;
+        const uint64_t b = (uint64_t)0xCD9E8D57u * c2;
+        const uint32_t n0 = (uint32_t)(b >> 32) ^ c1 ^ rk.k[2 * r];
+        const uint32_t n2 = (uint32_t)(a >> 32) ^ c3 ^ rk.k[2 * r + 1];
+        c1 = (uint32_t)b;
+        c3 = (uint32_t)a;
+        c0 = n0;
+        c2 = n2;
+    }
+    return U4{c0, c1, c2, c3};
+}
+
 // ---------------------------------------------------------------- graph
 // Device copy of the caller's CSR.  Edges keep the caller's order, so the
 // edge id of the coin definition is the position in these arrays.

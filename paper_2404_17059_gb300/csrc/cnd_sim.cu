@@ -56,7 +56,7 @@ struct Frontier {
     uint16_t *pw = nullptr;    // [n*B] pool: word index
     uint64_t *pb = nullptr;    // [n*B] pool: frontier bits
     int2 *work = nullptr;      // [work_cap] (slot, first edge of the item within the row)
-    int32_t *cnt = nullptr;    // device [4]: slots, work items, pool pairs, listed nodes
+    int32_t *cnt = nullptr;    // device [4]: pool pairs, slots (one 64-bit word), work items, listed nodes
 };
 
 struct Params {
@@ -65,12 +65,13 @@ struct Params {
     const int32_t *row_ptr;
     const uint2 *edge;         // {col, IC threshold} or {col, LT weight}
     uint64_t *vis, *nxt, *dmask;
+    uint64_t *cvt;             // LT: [v*nq+q] bit w%64 set <=> acc row (v, w) holds ~theta + sum
     uint32_t *acc;
     uint32_t *mark;            // [n] last stamp that listed the node
     int32_t *list;             // [n] nodes listed by the current step's push
     Frontier in, out;          // out.cnt[3] counts `list`
     uint32_t stamp;
-    uint32_t k0, k1;           // Philox key
+    RoundKeys rk;              // Philox round keys of rng_seed
     uint64_t g_base;           // trial-block index (trial >> 2) of bit 0 of word 0
     unsigned long long *level_counts;
     int32_t lc_len;
@@ -116,14 +117,14 @@ __device__ __forceinline__ int nth_set_bit(uint64_t x, int r) {
 
 // IC: bits of `c` (trials of one word) whose edge e is live.  Coins come in
 // blocks of four trials, one Philox call per block that has a bit in c.
-__device__ __forceinline__ uint64_t ic_live_bits(uint32_t e, uint64_t g0, uint64_t c, uint32_t thr, uint32_t k0,
-                                                 uint32_t k1, uint32_t &draws) {
+__device__ __forceinline__ uint64_t ic_live_bits(uint32_t e, uint64_t g0, uint64_t c, uint32_t thr,
+                                                 const RoundKeys &rk, uint32_t &draws) {
     uint64_t live = 0;
     while (c) {
         ++draws;
         const int j = (__ffsll((long long)c) - 1) >> 2;
         const uint64_t g = g0 + (uint64_t)j;
-        const U4 r = philox4x32_10(e, (uint32_t)g, 0u, (uint32_t)(g >> 32), k0, k1);
+        const U4 r = philox4x32_10(e, (uint32_t)g, 0u, (uint32_t)(g >> 32), rk);
         const uint32_t nib = (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
                              ((uint32_t)(r.w < thr) << 3);
         live |= (uint64_t)nib << (4 * j);
@@ -189,135 +190,160 @@ __device__ __forceinline__ int word_at(const uint64_t (&dm)[4], int r) {
     return 0;
 }
 
-// Warps take the listed nodes 32 at a time (one per lane), size and place
-// their slots, pool pairs and work items with one atomic per counter per 32
-// nodes, then collect each node's words cooperatively.
+// Placement of the slots of the nodes a block finalizes together: a block
+// scan gives each node its slot, pool offset and first work item, with one
+// 64-bit atomic for (slots, pool pairs) and one for work items per block
+// iteration.  cnt = {pool pairs, slots, work items, listed nodes}; the pool
+// count stays below 2^31 (n * B < 2^31), so it never carries into the slots.
+constexpr int kNPW = 2;                 // nodes per warp per block iteration
+constexpr int kNPB = kWarps * kNPW;     // nodes per block iteration
+
+// Block-cooperative finalize: each warp takes kNPW listed nodes per block
+// iteration, collects their words with frontier bits into slots, and emits
+// their work items.
 //   MODE 0 (seeds): every valid word, vis set to the valid mask.
 //   MODE 1 (IC):    the dirty words of nxt, cleared on the way.
-//   MODE 2 (LT):    threshold test of the touched trials of the dirty words;
-//                   the words with new activations go to the slot.
+//   MODE 2 (LT):    rows touched for the first time in this pass are converted
+//                   (64 thresholds drawn once; acc = sum + ~theta; activation
+//                   where sum > theta); rows converted earlier carry the
+//                   activations their push detected.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
+    __shared__ int s_kept[kNPB], s_nch[kNPB];
+    __shared__ int s_off[kNPB], s_slot[kNPB], s_wb[kNPB];
     const int lane = lane_id();
+    const int wid = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
     const int count = p.out.cnt[3];
-    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int B = p.B, nq = p.nq;
     unsigned long long pc = 0;
     uint32_t n_dr = 0;
-    for (int base = warp * 32; base < count; base += n_warps * 32) {
-        const int i = base + lane;
-        const bool act = i < count;
-        const int v = act ? p.list[i] : 0;
-        uint64_t dm[4] = {0ull, 0ull, 0ull, 0ull};
-        int K = 0;
-        if (act) {
-            if (MODE == 0) {
-                K = p.nvalid;
-            } else {
+    for (int base = blockIdx.x * kNPB; base < count; base += gridDim.x * kNPB) {
+        int vv[kNPW], KK[kNPW];
+        uint64_t dm[kNPW][4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (q < nq) {
-                        dm[q] = p.dmask[(size_t)v * nq + q];
-                        p.dmask[(size_t)v * nq + q] = 0ull;
-                        K += __popcll(dm[q]);
-                    }
+        for (int h = 0; h < kNPW; ++h) {
+            const int i = base + wid * kNPW + h;
+            const bool act = i < count;
+            vv[h] = act ? p.list[i] : 0;
+            KK[h] = 0;
+            dm[h][0] = dm[h][1] = dm[h][2] = dm[h][3] = 0ull;
+            if (!act) continue;
+            if (MODE == 0) {
+                KK[h] = p.nvalid;
+                continue;
+            }
+            const uint64_t mine = (lane < nq) ? p.dmask[(size_t)vv[h] * nq + lane] : 0ull;
+            if (lane < nq) p.dmask[(size_t)vv[h] * nq + lane] = 0ull;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                dm[h][q] = __shfl_sync(kFull, mine, q);
+                KK[h] += __popcll(dm[h][q]);
             }
         }
-        int kept = K;
-        if (MODE == 2) {
-            // threshold test, node by node; the result bits replace the touched
-            // bits in nxt until the copy below
-            kept = 0;
-            for (int s = 0; s < 32; ++s) {
-                const int Ks = __shfl_sync(kFull, K, s);
-                if (Ks == 0) continue;
-                const int vs = __shfl_sync(kFull, v, s);
-                uint64_t dms[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q) dms[q] = __shfl_sync(kFull, dm[q], s);
-                int kc = 0;
-                for (int r0 = 0; r0 < Ks; r0 += 32) {
+        for (int h = 0; h < kNPW; ++h) {
+            const int v = vv[h], K = KK[h];
+            int kept = K;
+            if (MODE == 2 && K > 0) {
+                kept = 0;
+                for (int r0 = 0; r0 < K; r0 += 32) {
                     const int r = r0 + lane;
                     uint64_t nb = 0;
-                    if (r < Ks) {
-                        const int w = word_at(dms, r);
-                        const size_t idx = (size_t)vs * B + w;
-                        const uint64_t vis = p.vis[idx];
-                        uint64_t cand = p.nxt[idx] & ~vis;
-                        const uint32_t *a = p.acc + idx * 64;
-                        while (cand) {
-                            ++n_dr;
-                            const int j = (__ffsll((long long)cand) - 1) >> 2;
-                            const uint64_t g = p.g_base + 16ull * w + (uint64_t)j;
-                            const U4 th = philox4x32_10((uint32_t)vs, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.k0, p.k1);
-                            const int b0 = 4 * j;
-                            const uint4 av = *reinterpret_cast<const uint4 *>(a + b0);
-                            uint64_t hit = (uint64_t)(av.x > th.x) | ((uint64_t)(av.y > th.y) << 1) |
-                                           ((uint64_t)(av.z > th.z) << 2) | ((uint64_t)(av.w > th.w) << 3);
-                            nb |= (hit << b0) & cand;
-                            cand &= ~(0xFull << b0);
+                    if (r < K) {
+                        const int w = word_at(dm[h], r);
+                        const size_t idx = (size_t)v * B + w;
+                        const uint64_t x = p.nxt[idx];
+                        uint64_t *cw = p.cvt + (size_t)v * nq + (w >> 6);
+                        if ((*cw >> (w & 63)) & 1ull) {
+                            nb = x;
+                        } else {
+                            const uint64_t vis = p.vis[idx];
+                            uint4 *a4 = reinterpret_cast<uint4 *>(p.acc + idx * 64);
+                            const uint64_t g0 = p.g_base + 16ull * w;
+#pragma unroll 2
+                            for (int j = 0; j < 16; ++j) {
+                                ++n_dr;
+                                const uint64_t g = g0 + (uint64_t)j;
+                                const U4 th = philox4x32_10((uint32_t)v, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.rk);
+                                uint4 s4 = a4[j];
+                                const uint64_t hit = (uint64_t)(s4.x > th.x) | ((uint64_t)(s4.y > th.y) << 1) |
+                                                     ((uint64_t)(s4.z > th.z) << 2) | ((uint64_t)(s4.w > th.w) << 3);
+                                nb |= hit << (4 * j);
+                                s4.x += ~th.x;
+                                s4.y += ~th.y;
+                                s4.z += ~th.z;
+                                s4.w += ~th.w;
+                                a4[j] = s4;
+                            }
+                            nb &= ~vis;
+                            if (nb) p.vis[idx] = vis | nb;
+                            atomicOr((unsigned long long *)cw, 1ull << (w & 63));
                         }
-                        if (nb) p.vis[idx] = vis | nb;
                         p.nxt[idx] = nb;
                         pc += __popcll(nb);
                     }
-                    kc += __popc(__ballot_sync(kFull, nb != 0ull));
+                    kept += __popc(__ballot_sync(kFull, nb != 0ull));
                 }
-                if (lane == s) kept = kc;
+            }
+            const int deg = kept > 0 ? p.row_ptr[v + 1] - p.row_ptr[v] : 0;
+            const int ne = edges_per_item(p, kept);
+            if (lane == 0) {
+                s_kept[wid * kNPW + h] = kept;
+                s_nch[wid * kNPW + h] = deg > 0 ? (deg + ne - 1) / ne : 0;
             }
         }
-        // places for the 32 nodes: inclusive warp scans of pairs, slots, items
-        const int has = kept > 0 ? 1 : 0;
-        const int deg = has ? p.row_ptr[v + 1] - p.row_ptr[v] : 0;
-        const int ne = edges_per_item(p, kept);
-        const int nch = deg > 0 ? (deg + ne - 1) / ne : 0;
-        int sk = kept, sh = has, sc = nch;
+        __syncthreads();
+        if (wid == 0) {
+            const int kk = lane < kNPB ? s_kept[lane] : 0;
+            const int hs = kk > 0 ? 1 : 0;
+            const int cc = lane < kNPB ? s_nch[lane] : 0;
+            int sk = kk, sh = hs, sc = cc;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int a1 = __shfl_up_sync(kFull, sk, o), a2 = __shfl_up_sync(kFull, sh, o),
-                      a3 = __shfl_up_sync(kFull, sc, o);
-            if (lane >= o) {
-                sk += a1;
-                sh += a2;
-                sc += a3;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int a1 = __shfl_up_sync(kFull, sk, o), a2 = __shfl_up_sync(kFull, sh, o),
+                          a3 = __shfl_up_sync(kFull, sc, o);
+                if (lane >= o) {
+                    sk += a1;
+                    sh += a2;
+                    sc += a3;
+                }
+            }
+            unsigned long long ps0 = 0;
+            int item0 = 0;
+            if (lane == 31) {
+                if (sk) ps0 = atomicAdd((unsigned long long *)p.out.cnt, ((unsigned long long)sh << 32) | (unsigned)sk);
+                if (sc) item0 = atomicAdd(&p.out.cnt[2], sc);
+            }
+            ps0 = __shfl_sync(kFull, ps0, 31);
+            item0 = __shfl_sync(kFull, item0, 31);
+            if (lane < kNPB) {
+                s_off[lane] = (int)(uint32_t)ps0 + sk - kk;
+                s_slot[lane] = (int)(ps0 >> 32) + sh - hs;
+                s_wb[lane] = item0 + sc - cc;
             }
         }
-        int pool0 = 0, slot0 = 0, item0 = 0;
-        if (lane == 31) {
-            if (sk) pool0 = atomicAdd(&p.out.cnt[2], sk);
-            if (sh) slot0 = atomicAdd(&p.out.cnt[0], sh);
-            if (sc) item0 = atomicAdd(&p.out.cnt[1], sc);
-        }
-        pool0 = __shfl_sync(kFull, pool0, 31);
-        slot0 = __shfl_sync(kFull, slot0, 31);
-        item0 = __shfl_sync(kFull, item0, 31);
-        const int off = pool0 + sk - kept, slot = slot0 + sh - has, wb = item0 + sc - nch;
-        if (has) {
-            p.out.node[slot] = v;
-            p.out.poff[slot] = off;
-            p.out.pk[slot] = kept;
-        }
-        // copy the words of each node with a slot, and emit its work items
-        unsigned todo = __ballot_sync(kFull, has);
-        while (todo) {
-            const int s = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int Ks = __shfl_sync(kFull, K, s);
-            const int vs = __shfl_sync(kFull, v, s);
-            const int offs = __shfl_sync(kFull, off, s);
-            uint64_t dms[4];
+        __syncthreads();
 #pragma unroll
-            for (int q = 0; q < 4; ++q) dms[q] = __shfl_sync(kFull, dm[q], s);
+        for (int h = 0; h < kNPW; ++h) {
+            const int e = wid * kNPW + h;
+            const int kept = s_kept[e];
+            if (kept == 0) continue;
+            const int v = vv[h], K = KK[h];
+            const int off = s_off[e], slot = s_slot[e];
+            if (lane == 0) {
+                p.out.node[slot] = v;
+                p.out.poff[slot] = off;
+                p.out.pk[slot] = kept;
+            }
             int pos = 0;
-            for (int r0 = 0; r0 < Ks; r0 += 32) {
+            for (int r0 = 0; r0 < K; r0 += 32) {
                 const int r = r0 + lane;
                 uint64_t x = 0;
                 int w = 0;
-                if (r < Ks) {
-                    w = MODE == 0 ? r : word_at(dms, r);
-                    const size_t idx = (size_t)vs * B + w;
+                if (r < K) {
+                    w = MODE == 0 ? r : word_at(dm[h], r);
+                    const size_t idx = (size_t)v * B + w;
                     if (MODE == 0) {
                         x = p.valid[w];
                         p.vis[idx] = x;
@@ -330,16 +356,14 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
                 const unsigned bm = __ballot_sync(kFull, x != 0ull);
                 if (x) {
                     const int q = pos + __popc(bm & below);
-                    p.out.pw[offs + q] = (uint16_t)w;
-                    p.out.pb[offs + q] = x;
+                    p.out.pw[off + q] = (uint16_t)w;
+                    p.out.pb[off + q] = x;
                 }
                 pos += __popc(bm);
             }
-            const int ncs = __shfl_sync(kFull, nch, s);
-            const int nes = __shfl_sync(kFull, ne, s);
-            const int sls = __shfl_sync(kFull, slot, s);
-            const int wbs = __shfl_sync(kFull, wb, s);
-            for (int c = lane; c < ncs; c += 32) p.out.work[wbs + c] = make_int2(sls, c * nes);
+            const int nch = s_nch[e], wb = s_wb[e];
+            const int ne = edges_per_item(p, kept);
+            for (int c = lane; c < nch; c += 32) p.out.work[wb + c] = make_int2(slot, c * ne);
         }
     }
     add_level_count(p, pc);
@@ -357,7 +381,7 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
     const int lane = lane_id();
     const int wid = threadIdx.x >> 5;
     ListBuf lb{s_list[wid], 0};
-    const int n_work = p.in.cnt[1];
+    const int n_work = p.in.cnt[2];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     const int B = p.B;
@@ -404,7 +428,7 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
                         if (c) {
                             uint64_t nb = c;
                             if (thr != kAlways)
-                                nb &= ic_live_bits((uint32_t)e, p.g_base + 16ull * w, c, thr, p.k0, p.k1, n_dr);
+                                nb &= ic_live_bits((uint32_t)e, p.g_base + 16ull * w, c, thr, p.rk, n_dr);
                             if (nb) {
                                 nb &= ~(uint64_t)atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)nb);
                                 if (nb) {
@@ -421,18 +445,50 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
                     const uint32_t wt = ed.y;
                     if (wt != 0u) {
                         ++n_wc;
-                        uint64_t c = f & ~(uint64_t)__ldg((const unsigned long long *)p.vis + idx);
+                        uint64_t c = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
                         if (c) {
                             n_up += __popcll(c);
-                            const uint64_t old = atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)c);
-                            mark_dirty(p, v, w, old);
                             uint32_t *a = p.acc + idx * 64;
-                            while (c) {
-                                const int b = __ffsll((long long)c) - 1;
-                                c &= c - 1;
-                                atomicAdd(a + b, wt);
+                            const bool conv = (__ldg((const unsigned long long *)p.cvt + (size_t)v * p.nq + (w >> 6)) >>
+                                               (w & 63)) & 1ull;
+                            if (!conv) {
+                                // first touches of the row: plain sums, converted by the finalize
+                                const uint64_t old =
+                                    atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)c);
+                                mark_dirty(p, v, w, old);
+                                while (c) {
+                                    const int b = __ffsll((long long)c) - 1;
+                                    c &= c - 1;
+                                    atomicAdd(a + b, wt);
+                                }
+                                hit = true;
+                            } else {
+                                // acc = ~theta + sum: the add that carries out of 32 bits is the
+                                // one that lifts the sum above theta (at most one carry ever,
+                                // since in-weights sum to at most 2^32 - 1)
+                                uint64_t nb = 0;
+                                while (c) {
+                                    int bb[4];
+                                    uint32_t ob[4];
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) {
+                                        bb[q] = c ? __ffsll((long long)c) - 1 : -1;
+                                        if (c) c &= c - 1;
+                                    }
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q) ob[q] = bb[q] >= 0 ? atomicAdd(a + bb[q], wt) : 0u;
+#pragma unroll
+                                    for (int q = 0; q < 4; ++q)
+                                        if (bb[q] >= 0 && ob[q] + wt < ob[q]) nb |= 1ull << bb[q];
+                                }
+                                if (nb) {
+                                    atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)nb);
+                                    const uint64_t old =
+                                        atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)nb);
+                                    mark_dirty(p, v, w, old);
+                                    hit = true;
+                                }
                             }
-                            hit = true;
                         }
                     }
                 }
@@ -673,6 +729,7 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         int64_t bmax = o.word_bits ? o.word_bits / 64 : kMaxB;
         bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)(budget / per_word)));
         bmax = std::min<int64_t>(bmax, kMaxB);
+        bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)0x7FFFFFFF / std::max(n, 1)));
         const int64_t n_pass = (total_words + bmax - 1) / bmax;
         const int B = (int)((total_words + n_pass - 1) / n_pass);
         const int nq = (B + 63) / 64;
@@ -690,8 +747,7 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         P.chunk = std::min(o.chunk_edges, 16384);
         P.row_ptr = G.row_ptr;
         P.edge = edge;
-        P.k0 = (uint32_t)rng_seed;
-        P.k1 = (uint32_t)(rng_seed >> 32);
+        P.rk = round_keys(rng_seed);
         P.level_counts = d_lc;
         P.lc_len = lc_len;
         uint64_t *d_valid = nullptr;
@@ -702,7 +758,10 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         CND_CUDA_TRY(W.alloc(&P.mark, (size_t)n));
         CND_CUDA_TRY(W.alloc(&P.list, (size_t)n));
         CND_CUDA_TRY(W.alloc(&d_valid, (size_t)B));
-        if (model == 1) CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
+        if (model == 1) {
+            CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
+            CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
+        }
         for (int i = 0; i < 2; ++i) {
             CND_CUDA_TRY(W.alloc(&fr[i].node, (size_t)n));
             CND_CUDA_TRY(W.alloc(&fr[i].poff, (size_t)n));
@@ -747,7 +806,10 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
             P.nvalid = (int32_t)nw_here;
             CND_CUDA_TRY(cudaMemcpyAsync(d_valid, valid.data(), sizeof(uint64_t) * B, cudaMemcpyHostToDevice, st));
             CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
-            if (model == 1) CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
+            if (model == 1) {
+                CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
+                CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, st));
+            }
             P.g_base = (uint64_t)(o.first_trial + 64 * w0) >> 2;
 
             // step 0: seeds
@@ -760,7 +822,7 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
                 k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, G.num_sms * 8)), 256, 0, st>>>(
                     P, d_seeds, n_seeds, d_bad);
                 CND_CUDA_TRY(cudaGetLastError());
-                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for(n_seeds, seed_blocks), st, P));
+                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for((n_seeds + kNPW - 1) / kNPW, seed_blocks), st, P));
                 launches += 2;
             }
             for (int L = 0;; ++L) {
@@ -770,7 +832,7 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
                     const cnd_status ts = collect_timing();
                     if (ts != CND_OK) return ts;
                 }
-                const int32_t slots = hcnt[0], items = hcnt[1];
+                const int32_t slots = hcnt[1], items = hcnt[2];
                 if (S) {
                     S->frontier_slots += slots;
                     S->work_items += items;
@@ -1055,8 +1117,7 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
         P.chunk = 0;
         P.row_ptr = G.row_ptr;
         P.edge = G.ic_edge;
-        P.k0 = (uint32_t)rng_seed;
-        P.k1 = (uint32_t)(rng_seed >> 32);
+        P.rk = round_keys(rng_seed);
         P.level_counts = nullptr;
         P.lc_len = 0;
         P.valid = d_valid;
@@ -1090,19 +1151,19 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
                 k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, G.num_sms * 8)), 256, 0, st>>>(
                     P, seeds, n_seeds, d_bad);
                 CND_CUDA_TRY(cudaGetLastError());
-                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for(n_seeds, seed_blocks), st, P));
+                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for((n_seeds + kNPW - 1) / kNPW, seed_blocks), st, P));
             }
             for (;;) {
                 CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
                 CND_CUDA_TRY(cudaStreamSynchronize(st));
-                if (hcnt[0] == 0 || hcnt[1] == 0) break;
+                if (hcnt[1] == 0 || hcnt[2] == 0) break;
                 const int nx = cur ^ 1;
                 CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
                 P.in = fr[cur];
                 P.out = fr[nx];
                 P.stamp = stamp++;
                 P.level += 1;
-                CND_CUDA_TRY(launch((const void *)k_push<0>, blocks_for(hcnt[1], push_blocks), st, P));
+                CND_CUDA_TRY(launch((const void *)k_push<0>, blocks_for(hcnt[2], push_blocks), st, P));
                 CND_CUDA_TRY(launch((const void *)k_finalize<1>, fin_blocks, st, P));
                 cur = nx;
             }
