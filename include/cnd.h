@@ -122,10 +122,18 @@ typedef struct cnd_sim_opts {
     int32_t pull_permille;     /* AUTO: pull when the frontier's out-edges exceed this many
                                   thousandths of m; 0 = built-in default */
     int32_t chunk_edges;       /* edges per push work item (0 = automatic) */
-    int32_t reserved0;
+    int32_t defer_bits;        /* > 0: a node's word with fewer newly active trials than this may
+                                  wait for more before its out-edges are examined; the spreads,
+                                  counts and edge checks are unchanged (IC: reachability, LT: the
+                                  least fixed point do not depend on the order of expansion), but
+                                  steps no longer are activation times, so level counts and
+                                  max_levels are refused (CND_EINVAL); 0 = off, at most 64 */
     double timeout_s;          /* > 0: give up with CND_ETIMEOUT after this many seconds */
     cnd_sim_stats *stats;      /* NULL or host struct filled by the call */
-    int64_t reserved[3];
+    int32_t defer_steps;       /* with defer_bits: a word waits at most this many steps (0 = until
+                                  nothing else is left to expand) */
+    int32_t reserved1;
+    int64_t reserved[2];
 } cnd_sim_opts;
 
 void cnd_sim_opts_init(cnd_sim_opts *opts);

@@ -74,10 +74,12 @@ class cnd_sim_opts(C.Structure):
         ("level_counts_len", C.c_int32),
         ("pull_permille", C.c_int32),
         ("chunk_edges", C.c_int32),
-        ("reserved0", C.c_int32),
+        ("defer_bits", C.c_int32),
         ("timeout_s", C.c_double),
         ("stats", C.c_void_p),
-        ("reserved", C.c_int64 * 3),
+        ("defer_steps", C.c_int32),
+        ("reserved1", C.c_int32),
+        ("reserved", C.c_int64 * 2),
     ]
 
 
@@ -206,7 +208,8 @@ class SimResult:
 
 def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=True, node_count=True,
               first_trial=0, max_levels=0, direction="auto", word_bits=0, level_counts_len=0,
-              edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None, stats=0):
+              edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None, stats=0,
+              defer_bits=0, defer_steps=0):
     L = load()
     n_trials = int(n_trials)
     dev = _is_torch_cuda(seeds)
@@ -250,6 +253,8 @@ def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=Tru
         o.level_counts_len = int(level_counts_len)
         o.pull_permille = int(pull_permille)
         o.chunk_edges = int(chunk_edges)
+        o.defer_bits = int(defer_bits)
+        o.defer_steps = int(defer_steps)
         o.timeout_s = float(timeout_s)
         stt = None
         if stats:

@@ -68,9 +68,14 @@ struct Params {
     uint64_t *cvt;             // LT: [v*nq+q] bit w%64 set <=> acc row (v, w) holds ~theta + sum
     uint32_t *acc;
     uint32_t *mark;            // [n] last stamp that listed the node
-    int32_t *list;             // [n] nodes listed by the current step's push
-    Frontier in, out;          // out.cnt[3] counts `list`
-    uint32_t stamp;
+    int32_t *lin, *lin_cnt;    // [n] nodes the current step finalizes (its push lists them here)
+    int32_t *lnext, *lnext_cnt;// [n] nodes whose words wait for the next step (deferral)
+    Frontier in, out;
+    uint32_t stamp;            // stamp of the current step; stamp + 1 is the next step's
+    int32_t tau;               // > 0: words with fewer new bits than tau may wait (not when force)
+    int32_t max_wait;          // > 0: ... for at most max_wait steps
+    uint8_t *age;              // [n*B] steps the word has waited (deferral)
+    int32_t force;             // 1: expand every pending word
     RoundKeys rk;              // Philox round keys of rng_seed
     uint64_t g_base;           // trial-block index (trial >> 2) of bit 0 of word 0
     unsigned long long *level_counts;
@@ -142,9 +147,9 @@ struct ListBuf {
     __device__ __forceinline__ void flush(const Params &p) {
         __syncwarp();
         int base = 0;
-        if (lane_id() == 0) base = atomicAdd(&p.out.cnt[3], n);
+        if (lane_id() == 0) base = atomicAdd(p.lin_cnt, n);
         base = __shfl_sync(kFull, base, 0);
-        for (int j = lane_id(); j < n; j += 32) p.list[base + j] = buf[j];
+        for (int j = lane_id(); j < n; j += 32) p.lin[base + j] = buf[j];
         __syncwarp();
         n = 0;
     }
@@ -174,7 +179,7 @@ __global__ void k_seed_select(Params p, const int32_t *__restrict__ seeds, int32
             atomicExch(bad, 1);
             continue;
         }
-        if (atomicExch(&p.mark[s], p.stamp) != p.stamp) p.list[atomicAdd(&p.out.cnt[3], 1)] = s;
+        if (atomicExch(&p.mark[s], p.stamp) != p.stamp) p.lin[atomicAdd(p.lin_cnt, 1)] = s;
     }
 }
 
@@ -202,20 +207,25 @@ constexpr int kNPB = kWarps * kNPW;     // nodes per block iteration
 // iteration, collects their words with frontier bits into slots, and emits
 // their work items.
 //   MODE 0 (seeds): every valid word, vis set to the valid mask.
-//   MODE 1 (IC):    the dirty words of nxt, cleared on the way.
+//   MODE 1 (IC):    the dirty words of nxt (new activations).
 //   MODE 2 (LT):    rows touched for the first time in this pass are converted
 //                   (64 thresholds drawn once; acc = sum + ~theta; activation
 //                   where sum > theta); rows converted earlier carry the
 //                   activations their push detected.
+// With deferral (tau > 0, not force) a word with fewer than tau new bits stays
+// in nxt, still dirty, and its node is listed for the next step: expanding it
+// later, merged with later bits, leaves reachability (IC) and the least fixed
+// point (LT) unchanged.
 template <int MODE>
 __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
-    __shared__ int s_kept[kNPB], s_nch[kNPB];
-    __shared__ int s_off[kNPB], s_slot[kNPB], s_wb[kNPB];
+    __shared__ int s_kept[kNPB], s_nch[kNPB], s_def[kNPB];
+    __shared__ int s_off[kNPB], s_slot[kNPB], s_wb[kNPB], s_dpos[kNPB];
     const int lane = lane_id();
     const int wid = threadIdx.x >> 5;
     const unsigned below = (1u << lane) - 1u;
-    const int count = p.out.cnt[3];
+    const int count = *p.lin_cnt;
     const int B = p.B, nq = p.nq;
+    const int tau = (MODE == 0 || p.force) ? 0 : p.tau;
     unsigned long long pc = 0;
     uint32_t n_dr = 0;
     for (int base = blockIdx.x * kNPB; base < count; base += gridDim.x * kNPB) {
@@ -225,7 +235,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
         for (int h = 0; h < kNPW; ++h) {
             const int i = base + wid * kNPW + h;
             const bool act = i < count;
-            vv[h] = act ? p.list[i] : 0;
+            vv[h] = act ? p.lin[i] : 0;
             KK[h] = 0;
             dm[h][0] = dm[h][1] = dm[h][2] = dm[h][3] = 0ull;
             if (!act) continue;
@@ -244,46 +254,63 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
 #pragma unroll
         for (int h = 0; h < kNPW; ++h) {
             const int v = vv[h], K = KK[h];
-            int kept = K;
-            if (MODE == 2 && K > 0) {
+            int kept = K, deferred = 0;
+            if (MODE != 0 && K > 0) {
+                // the new bits of every listed word (LT: after the threshold test);
+                // words that wait go back into the dirty mask
                 kept = 0;
                 for (int r0 = 0; r0 < K; r0 += 32) {
                     const int r = r0 + lane;
                     uint64_t nb = 0;
+                    int w = 0;
                     if (r < K) {
-                        const int w = word_at(dm[h], r);
+                        w = word_at(dm[h], r);
                         const size_t idx = (size_t)v * B + w;
                         const uint64_t x = p.nxt[idx];
-                        uint64_t *cw = p.cvt + (size_t)v * nq + (w >> 6);
-                        if ((*cw >> (w & 63)) & 1ull) {
+                        if (MODE == 1) {
                             nb = x;
                         } else {
-                            const uint64_t vis = p.vis[idx];
-                            uint4 *a4 = reinterpret_cast<uint4 *>(p.acc + idx * 64);
-                            const uint64_t g0 = p.g_base + 16ull * w;
+                            uint64_t *cw = p.cvt + (size_t)v * nq + (w >> 6);
+                            if ((*cw >> (w & 63)) & 1ull) {
+                                nb = x;
+                            } else {
+                                const uint64_t vis = p.vis[idx];
+                                uint4 *a4 = reinterpret_cast<uint4 *>(p.acc + idx * 64);
+                                const uint64_t g0 = p.g_base + 16ull * w;
 #pragma unroll 2
-                            for (int j = 0; j < 16; ++j) {
-                                ++n_dr;
-                                const uint64_t g = g0 + (uint64_t)j;
-                                const U4 th = philox4x32_10((uint32_t)v, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.rk);
-                                uint4 s4 = a4[j];
-                                const uint64_t hit = (uint64_t)(s4.x > th.x) | ((uint64_t)(s4.y > th.y) << 1) |
-                                                     ((uint64_t)(s4.z > th.z) << 2) | ((uint64_t)(s4.w > th.w) << 3);
-                                nb |= hit << (4 * j);
-                                s4.x += ~th.x;
-                                s4.y += ~th.y;
-                                s4.z += ~th.z;
-                                s4.w += ~th.w;
-                                a4[j] = s4;
+                                for (int j = 0; j < 16; ++j) {
+                                    ++n_dr;
+                                    const uint64_t g = g0 + (uint64_t)j;
+                                    const U4 th =
+                                        philox4x32_10((uint32_t)v, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.rk);
+                                    uint4 s4 = a4[j];
+                                    const uint64_t hit = (uint64_t)(s4.x > th.x) | ((uint64_t)(s4.y > th.y) << 1) |
+                                                         ((uint64_t)(s4.z > th.z) << 2) |
+                                                         ((uint64_t)(s4.w > th.w) << 3);
+                                    nb |= hit << (4 * j);
+                                    s4.x += ~th.x;
+                                    s4.y += ~th.y;
+                                    s4.z += ~th.z;
+                                    s4.w += ~th.w;
+                                    a4[j] = s4;
+                                }
+                                nb &= ~vis;
+                                if (nb) p.vis[idx] = vis | nb;
+                                atomicOr((unsigned long long *)cw, 1ull << (w & 63));
                             }
-                            nb &= ~vis;
-                            if (nb) p.vis[idx] = vis | nb;
-                            atomicOr((unsigned long long *)cw, 1ull << (w & 63));
+                            p.nxt[idx] = nb;
                         }
-                        p.nxt[idx] = nb;
-                        pc += __popcll(nb);
                     }
-                    kept += __popc(__ballot_sync(kFull, nb != 0ull));
+                    bool wait = nb != 0ull && __popcll(nb) < tau;
+                    if (nb != 0ull && tau > 0 && p.max_wait > 0) {
+                        uint8_t *ag = p.age + (size_t)v * B + w;
+                        const int a = *ag;
+                        wait = wait && a < p.max_wait;
+                        *ag = wait ? (uint8_t)(a + 1) : (uint8_t)0;
+                    }
+                    if (wait) atomicOr((unsigned long long *)(p.dmask + (size_t)v * nq + (w >> 6)), 1ull << (w & 63));
+                    kept += __popc(__ballot_sync(kFull, nb != 0ull && !wait));
+                    deferred |= __any_sync(kFull, wait) ? 1 : 0;
                 }
             }
             const int deg = kept > 0 ? p.row_ptr[v + 1] - p.row_ptr[v] : 0;
@@ -291,6 +318,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
             if (lane == 0) {
                 s_kept[wid * kNPW + h] = kept;
                 s_nch[wid * kNPW + h] = deg > 0 ? (deg + ne - 1) / ne : 0;
+                s_def[wid * kNPW + h] = deferred;
             }
         }
         __syncthreads();
@@ -298,38 +326,48 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
             const int kk = lane < kNPB ? s_kept[lane] : 0;
             const int hs = kk > 0 ? 1 : 0;
             const int cc = lane < kNPB ? s_nch[lane] : 0;
-            int sk = kk, sh = hs, sc = cc;
+            const int dd = lane < kNPB ? s_def[lane] : 0;
+            int sk = kk, sh = hs, sc = cc, sd = dd;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const int a1 = __shfl_up_sync(kFull, sk, o), a2 = __shfl_up_sync(kFull, sh, o),
-                          a3 = __shfl_up_sync(kFull, sc, o);
+                          a3 = __shfl_up_sync(kFull, sc, o), a4 = __shfl_up_sync(kFull, sd, o);
                 if (lane >= o) {
                     sk += a1;
                     sh += a2;
                     sc += a3;
+                    sd += a4;
                 }
             }
             unsigned long long ps0 = 0;
-            int item0 = 0;
+            int item0 = 0, d0 = 0;
             if (lane == 31) {
                 if (sk) ps0 = atomicAdd((unsigned long long *)p.out.cnt, ((unsigned long long)sh << 32) | (unsigned)sk);
                 if (sc) item0 = atomicAdd(&p.out.cnt[2], sc);
+                if (sd) d0 = atomicAdd(p.lnext_cnt, sd);
             }
             ps0 = __shfl_sync(kFull, ps0, 31);
             item0 = __shfl_sync(kFull, item0, 31);
+            d0 = __shfl_sync(kFull, d0, 31);
             if (lane < kNPB) {
                 s_off[lane] = (int)(uint32_t)ps0 + sk - kk;
                 s_slot[lane] = (int)(ps0 >> 32) + sh - hs;
                 s_wb[lane] = item0 + sc - cc;
+                s_dpos[lane] = d0 + sd - dd;
             }
         }
         __syncthreads();
 #pragma unroll
         for (int h = 0; h < kNPW; ++h) {
             const int e = wid * kNPW + h;
+            const int v = vv[h], K = KK[h];
+            if (s_def[e] && lane == 0) {
+                // the node's waiting words are expanded by a later step
+                p.mark[v] = p.stamp + 1u;
+                p.lnext[s_dpos[e]] = v;
+            }
             const int kept = s_kept[e];
             if (kept == 0) continue;
-            const int v = vv[h], K = KK[h];
             const int off = s_off[e], slot = s_slot[e];
             if (lane == 0) {
                 p.out.node[slot] = v;
@@ -349,9 +387,11 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
                         p.vis[idx] = x;
                     } else {
                         x = p.nxt[idx];
-                        p.nxt[idx] = 0ull;
+                        // a word that waits got its dirty bit back in the pass above
+                        if (tau > 0 && ((p.dmask[(size_t)v * nq + (w >> 6)] >> (w & 63)) & 1ull)) x = 0ull;
+                        else p.nxt[idx] = 0ull;
                     }
-                    if (MODE != 2) pc += __popcll(x);
+                    pc += __popcll(x);
                 }
                 const unsigned bm = __ballot_sync(kFull, x != 0ull);
                 if (x) {
@@ -633,8 +673,13 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
     if (n_seeds < 0 || (n_seeds > 0 && !seeds) || n_trials < 0 || n_trials > 0x7FFFFFFFll || o.first_trial < 0 ||
         (o.first_trial & 63) || o.word_bits < 0 || (o.word_bits & 63) || o.word_bits > 64 * kMaxB ||
         o.level_counts_len < 0 || (o.level_counts_len > 0 && !o.level_counts_out) || o.chunk_edges < 0 ||
-        o.direction < 0 || o.direction > 2) {
-        set_error("%s: bad arguments (n_seeds, n_trials, first_trial %% 64, word_bits, level_counts, chunk)", fn);
+        o.direction < 0 || o.direction > 2 || o.defer_bits < 0 || o.defer_bits > 64) {
+        set_error("%s: bad arguments (n_seeds, n_trials, first_trial %% 64, word_bits, level_counts, chunk, defer_bits)",
+                  fn);
+        return CND_EINVAL;
+    }
+    if (o.defer_bits > 0 && (o.level_counts_len > 0 || o.max_levels > 0)) {
+        set_error("%s: defer_bits changes activation steps; it cannot be combined with level counts or max_levels", fn);
         return CND_EINVAL;
     }
     const bool dev = o.device_ptrs != 0;
@@ -756,8 +801,17 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         CND_CUDA_TRY(W.alloc(&P.nxt, nB));
         CND_CUDA_TRY(W.alloc(&P.dmask, (size_t)n * nq));
         CND_CUDA_TRY(W.alloc(&P.mark, (size_t)n));
-        CND_CUDA_TRY(W.alloc(&P.list, (size_t)n));
+        int32_t *lists[2] = {nullptr, nullptr}, *d_lcnt = nullptr;
+        CND_CUDA_TRY(W.alloc(&lists[0], (size_t)n));
+        CND_CUDA_TRY(W.alloc(&lists[1], (size_t)n));
+        CND_CUDA_TRY(W.alloc(&d_lcnt, 2));
         CND_CUDA_TRY(W.alloc(&d_valid, (size_t)B));
+        P.tau = o.defer_bits;
+        P.max_wait = o.defer_steps;
+        if (o.defer_bits > 0 && o.defer_steps > 0) {
+            CND_CUDA_TRY(W.alloc(&P.age, nB));
+            CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
+        }
         if (model == 1) {
             CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
             CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
@@ -780,7 +834,11 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
         CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
         CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
-        if (!t_pinned.h) CND_CUDA_TRY(cudaMallocHost(&t_pinned.h, 4 * sizeof(int32_t)));
+        if (!t_pinned.h) CND_CUDA_TRY(cudaMallocHost(&t_pinned.h, 6 * sizeof(int32_t)));
+        if (o.defer_steps < 0 || o.defer_steps > 255) {
+            set_error("%s: defer_steps must be in 0..255", fn);
+            return CND_EINVAL;
+        }
         int32_t *hcnt = t_pinned.h;
 
         const void *k_push_fn = model == 0 ? (const void *)k_push<0> : (const void *)k_push<1>;
@@ -806,16 +864,23 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
             P.nvalid = (int32_t)nw_here;
             CND_CUDA_TRY(cudaMemcpyAsync(d_valid, valid.data(), sizeof(uint64_t) * B, cudaMemcpyHostToDevice, st));
             CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
+            if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
             if (model == 1) {
                 CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
                 CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, st));
             }
             P.g_base = (uint64_t)(o.first_trial + 64 * w0) >> 2;
 
-            // step 0: seeds
+            // step 0: seeds (finalized from list 1; nothing waits afterwards)
             int cur = 0;
             CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 4 * sizeof(int32_t), st));
+            CND_CUDA_TRY(cudaMemsetAsync(d_lcnt, 0, 2 * sizeof(int32_t), st));
             P.out = fr[cur];
+            P.lin = lists[1];
+            P.lin_cnt = d_lcnt + 1;
+            P.lnext = lists[0];
+            P.lnext_cnt = d_lcnt;
+            P.force = 0;
             P.stamp = stamp++;
             P.level = 0;
             if (n_seeds > 0) {
@@ -827,22 +892,24 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
             }
             for (int L = 0;; ++L) {
                 CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+                CND_CUDA_TRY(cudaMemcpyAsync(hcnt + 4, d_lcnt + (L & 1), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
                 CND_CUDA_TRY(cudaStreamSynchronize(st));
                 if (timing) {
                     const cnd_status ts = collect_timing();
                     if (ts != CND_OK) return ts;
                 }
-                const int32_t slots = hcnt[1], items = hcnt[2];
+                // slots / work items of step L's frontier; nodes whose words wait
+                const int32_t slots = hcnt[1], items = hcnt[2], waiting = hcnt[4];
                 if (S) {
                     S->frontier_slots += slots;
                     S->work_items += items;
                 }
-                if (slots == 0) break;
+                if (slots == 0 && waiting == 0) break;
                 if (o.max_levels > 0 && L >= o.max_levels) {
                     limit_hit = true;
                     break;
                 }
-                if (items == 0) break;
+                if (items == 0 && waiting == 0) break;
                 if (o.timeout_s > 0) {
                     const double el =
                         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -854,12 +921,19 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
                 }
                 const int nx = cur ^ 1;
                 CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
+                CND_CUDA_TRY(cudaMemsetAsync(d_lcnt + ((L + 1) & 1), 0, sizeof(int32_t), st));
                 P.in = fr[cur];
                 P.out = fr[nx];
+                P.lin = lists[L & 1];
+                P.lin_cnt = d_lcnt + (L & 1);
+                P.lnext = lists[(L + 1) & 1];
+                P.lnext_cnt = d_lcnt + ((L + 1) & 1);
                 P.stamp = stamp++;
                 P.level = L + 1;
+                // nothing to expand in this step: every waiting word goes now
+                P.force = items == 0 ? 1 : 0;
                 if (timing) CND_CUDA_TRY(cudaEventRecord(ev.e[0], st));
-                CND_CUDA_TRY(launch(k_push_fn, blocks_for(items, push_blocks), st, P));
+                if (items > 0) CND_CUDA_TRY(launch(k_push_fn, blocks_for(items, push_blocks), st, P));
                 if (timing) {
                     CND_CUDA_TRY(cudaEventRecord(ev.e[1], st));
                     CND_CUDA_TRY(cudaEventRecord(ev.e[2], st));
@@ -1036,7 +1110,10 @@ static size_t place_static(Arena &a, Params &P, Frontier (&fr)[2], int32_t n, in
     P.nxt = a.take<uint64_t>(nB);
     P.dmask = a.take<uint64_t>((size_t)n * nq);
     P.mark = a.take<uint32_t>((size_t)n);
-    P.list = a.take<int32_t>((size_t)n);
+    P.lin = a.take<int32_t>((size_t)n);
+    P.lnext = a.take<int32_t>((size_t)n);
+    P.lin_cnt = a.take<int32_t>(2);
+    P.lnext_cnt = P.lin_cnt ? P.lin_cnt + 1 : nullptr;
     *d_valid = a.take<uint64_t>((size_t)B);
     *d_checks = a.take<unsigned long long>(1);
     *d_bad = a.take<int32_t>(1);
@@ -1115,6 +1192,9 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
         P.B = B;
         P.nq = nq;
         P.chunk = 0;
+        P.tau = 0;
+        P.max_wait = 0;
+        P.force = 0;
         P.row_ptr = G.row_ptr;
         P.edge = G.ic_edge;
         P.rk = round_keys(rng_seed);
@@ -1144,6 +1224,7 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
             P.g_base = (uint64_t)(64 * w0) >> 2;
             int cur = 0;
             CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 4 * sizeof(int32_t), st));
+            CND_CUDA_TRY(cudaMemsetAsync(P.lin_cnt, 0, 2 * sizeof(int32_t), st));
             P.out = fr[cur];
             P.stamp = stamp++;
             P.level = 0;
@@ -1159,6 +1240,7 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
                 if (hcnt[1] == 0 || hcnt[2] == 0) break;
                 const int nx = cur ^ 1;
                 CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
+                CND_CUDA_TRY(cudaMemsetAsync(P.lin_cnt, 0, sizeof(int32_t), st));
                 P.in = fr[cur];
                 P.out = fr[nx];
                 P.stamp = stamp++;

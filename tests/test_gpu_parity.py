@@ -218,3 +218,26 @@ def test_plain_entry_points(er0):
     a = P.cnd_lt_simulate(G, seeds, 500, 1)
     b = ref("lt", g, seeds, 500, 1, w=w)
     assert np.array_equal(a.spread, b.spread) and np.array_equal(a.node_count, b.node_count)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_deferred_expansion_same_results(ba, rmat14, model):
+    """Words that wait for more bits before expansion (defer_bits) change no result."""
+    for fx in (ba, rmat14):
+        g, G, p, w, seeds = fx
+        b = ref(model, g, seeds, 640, 3, p=p, w=w, level_counts_len=0)
+        for tau, ds in ((1, 0), (2, 0), (5, 0), (17, 0), (64, 0), (64, 1), (64, 3), (8, 2), (33, 255)):
+            a = sim(model, G, seeds, 640, 3, defer_bits=tau, defer_steps=ds, level_counts_len=0)
+            assert a.status == P.CND_OK
+            assert np.array_equal(a.spread, b.spread)
+            assert np.array_equal(a.node_count, b.node_count)
+            assert a.edge_checks == b.edge_checks
+
+
+def test_deferred_expansion_refuses_levels(er0):
+    g, G, p, w, seeds = er0
+    with pytest.raises(P.CndError) as ei:
+        sim("ic", G, seeds, 64, 1, defer_bits=4)  # level counts requested by default here
+    assert ei.value.status == P.CND_EINVAL
+    with pytest.raises(P.CndError):
+        sim("ic", G, seeds, 64, 1, defer_bits=4, level_counts_len=0, max_levels=3)
