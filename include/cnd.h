@@ -186,6 +186,31 @@ cnd_status cnd_lt_simulate_ex(const cnd_graph *g, const int32_t *seeds, int32_t 
                               const cnd_sim_opts *opts);
 
 /*
+ * Batched simulation: n_items independent problems in one call, each with its
+ * own seed set, trial count and key -- the workload of evaluating many
+ * candidate seed sets, e.g. the marginal gains of greedy / CELF influence
+ * maximisation (Sec. 2 "Influence Maximization").  Item i has seeds
+ * seeds[seed_off[i] .. seed_off[i+1]), trials 0 .. n_trials[i]-1 (plus
+ * opts->first_trial) and rng_seed[i]; its results are exactly those of
+ * cnd_ic_simulate / cnd_lt_simulate on that item alone.  The trials of all
+ * items are packed into shared passes (64-trial words of different items side
+ * by side), so small items keep the whole GPU busy.
+ *   seed_off (n_items+1 int64), n_trials (n_items int32, each 0 .. 2^31-1) and
+ *   rng_seed (n_items uint64) are host arrays whatever opts->device_ptrs says:
+ *   they drive the packing.  seeds and the outputs follow device_ptrs.
+ *   spread_out:     NULL or sum(n_trials) int32; trial t of item i is at
+ *                   n_trials[0] + ... + n_trials[i-1] + t.
+ *   node_count_out: NULL or n_items * n int32; row i counts item i's trials.
+ * Edge checks and level counts (opts) are summed over all items.
+ */
+cnd_status cnd_ic_simulate_batch(const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,
+                                 const int32_t *n_trials, const uint64_t *rng_seed, int32_t *spread_out,
+                                 int32_t *node_count_out, const cnd_sim_opts *opts);
+cnd_status cnd_lt_simulate_batch(const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,
+                                 const int32_t *n_trials, const uint64_t *rng_seed, int32_t *spread_out,
+                                 int32_t *node_count_out, const cnd_sim_opts *opts);
+
+/*
  * Weighted-cascade LT weights for a CSR graph (Sec. 4 "Benchmarks", WC model:
  * the weight of every edge entering v is 1/in-degree(v)) in fixed point:
  * w_out[e] = floor((2^32 - 1) / in-degree(col[e])), so in-weights sum to at

@@ -24,7 +24,8 @@ _DIRS = {"auto": CND_DIR_AUTO, "push": CND_DIR_PUSH, "pull": CND_DIR_PULL}
 EXPORTS = (
     "cnd_sim_opts_init", "cnd_graph_create", "cnd_graph_destroy", "cnd_graph_info", "cnd_ic_simulate",
     "cnd_lt_simulate", "cnd_ic_simulate_ex", "cnd_lt_simulate_ex", "cnd_lt_weights_wc",
-    "cnd_philox4x32_10", "cnd_last_error", "cnd_ic_simulate_noalloc",
+    "cnd_philox4x32_10", "cnd_last_error", "cnd_ic_simulate_noalloc", "cnd_ic_simulate_batch",
+    "cnd_lt_simulate_batch",
 )
 
 
@@ -117,6 +118,9 @@ def load(build_if_missing: bool = True):
             getattr(L, name).restype = i32
         for name in ("cnd_ic_simulate_ex", "cnd_lt_simulate_ex"):
             getattr(L, name).argtypes = [vp, vp, i32, i64, u64, vp, vp, C.POINTER(cnd_sim_opts)]
+            getattr(L, name).restype = i32
+        for name in ("cnd_ic_simulate_batch", "cnd_lt_simulate_batch"):
+            getattr(L, name).argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, C.POINTER(cnd_sim_opts)]
             getattr(L, name).restype = i32
         L.cnd_lt_weights_wc.argtypes = [i32, i32, vp, vp]
         L.cnd_lt_weights_wc.restype = i32
@@ -323,3 +327,69 @@ def cnd_ic_simulate_noalloc(g, seeds, n_trials, rng_seed, spread_out, node_count
         C.c_uint64(rng_seed), C.c_void_p(spread_out.data_ptr()) if int(n_trials) else None,
         C.c_void_p(node_count_out.data_ptr()), strm)
     return _check(st)
+
+
+def _simulate_batch(fn_name, g, seed_off, seeds, n_trials, rng_seed, *, spread=True, node_count=False,
+                    edge_checks=False, level_counts_len=0, stream=None, stats=0, **kw):
+    """Batch form: seed_off / n_trials / rng_seed are host arrays; seeds may be a CUDA tensor."""
+    L = load()
+    seed_off = np.ascontiguousarray(seed_off, dtype=np.int64)
+    n_trials = np.ascontiguousarray(n_trials, dtype=np.int32)
+    rng_seed = np.ascontiguousarray(rng_seed, dtype=np.uint64)
+    n_items = int(n_trials.shape[0])
+    total = int(n_trials.astype(np.int64).sum())
+    dev = _is_torch_cuda(seeds)
+    if dev:
+        import torch
+        seeds_t = seeds.to(torch.int32).contiguous()
+        sp = torch.empty(total, dtype=torch.int32, device=seeds.device) if spread else None
+        nc = torch.empty(n_items * g.n, dtype=torch.int32, device=seeds.device) if node_count else None
+        ec = torch.zeros(1, dtype=torch.int64, device=seeds.device) if edge_checks else None
+        lc = torch.zeros(level_counts_len, dtype=torch.int64, device=seeds.device) if level_counts_len else None
+        ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None and t.numel() else None  # noqa: E731
+        seeds_p, sp_p, nc_p = ptr(seeds_t), ptr(sp), ptr(nc)
+        ec_p = ec.data_ptr() if ec is not None else None
+        lc_p = lc.data_ptr() if lc is not None else None
+        strm = stream if stream is not None else torch.cuda.current_stream(seeds.device).cuda_stream
+    else:
+        seeds_a = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).ravel())
+        sp = np.empty(total, dtype=np.int32) if spread else None
+        nc = np.empty(n_items * g.n, dtype=np.int32) if node_count else None
+        ec = np.zeros(1, dtype=np.int64) if edge_checks else None
+        lc = np.zeros(level_counts_len, dtype=np.int64) if level_counts_len else None
+        seeds_p = _np_ptr(seeds_a) if seeds_a.size else None
+        sp_p = _np_ptr(sp) if sp is not None and total else None
+        nc_p = _np_ptr(nc)
+        ec_p = ec.ctypes.data if ec is not None else None
+        lc_p = lc.ctypes.data if lc is not None else None
+        strm = stream
+    o = cnd_sim_opts_init()
+    o.device_ptrs = 1 if dev else 0
+    o.stream = strm
+    o.edge_checks_out = ec_p
+    o.level_counts_out = lc_p
+    o.level_counts_len = int(level_counts_len)
+    for k, v in kw.items():
+        setattr(o, k, _DIRS[v] if k == "direction" and isinstance(v, str) else int(v) if k != "timeout_s" else float(v))
+    stt = None
+    if stats:
+        stt = cnd_sim_stats()
+        stt.flags = int(stats)
+        o.stats = C.cast(C.pointer(stt), C.c_void_p)
+    st = getattr(L, fn_name)(g.handle, n_items, _np_ptr(seed_off), seeds_p, _np_ptr(n_trials), _np_ptr(rng_seed),
+                             sp_p, nc_p, C.byref(o))
+    _check(st, allow=(CND_ELIMIT,))
+    ecv = None
+    if ec is not None:
+        ecv = int(ec[0].item()) if dev else int(ec[0])
+    if nc is not None:
+        nc = nc.reshape(n_items, g.n)
+    return SimResult(st, sp, nc, ecv, lc, stt.as_dict() if stt is not None else None)
+
+
+def cnd_ic_simulate_batch(g, seed_off, seeds, n_trials, rng_seed, **kw) -> SimResult:
+    return _simulate_batch("cnd_ic_simulate_batch", g, seed_off, seeds, n_trials, rng_seed, **kw)
+
+
+def cnd_lt_simulate_batch(g, seed_off, seeds, n_trials, rng_seed, **kw) -> SimResult:
+    return _simulate_batch("cnd_lt_simulate_batch", g, seed_off, seeds, n_trials, rng_seed, **kw)

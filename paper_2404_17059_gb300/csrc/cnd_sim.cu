@@ -76,7 +76,9 @@ struct Params {
     int32_t max_wait;          // > 0: ... for at most max_wait steps
     uint8_t *age;              // [n*B] steps the word has waited (deferral)
     int32_t force;             // 1: expand every pending word
-    RoundKeys rk;              // Philox round keys of rng_seed
+    RoundKeys rk;              // Philox round keys of rng_seed (all words share one key)
+    const uint2 *wkey;         // [B] per-word Philox key (batches: words of different items)
+    const uint64_t *wg0;       // [B] per-word trial-block index of bit 0
     uint64_t g_base;           // trial-block index (trial >> 2) of bit 0 of word 0
     unsigned long long *level_counts;
     int32_t lc_len;
@@ -120,16 +122,33 @@ __device__ __forceinline__ int nth_set_bit(uint64_t x, int r) {
     return 32 + (int)__fns((uint32_t)(x >> 32), 0, r - c + 1);
 }
 
-// IC: bits of `c` (trials of one word) whose edge e is live.  Coins come in
+// Philox block (index, trial block g, domain) of word w: one key for the whole
+// pass, or (batches) the key of the item that owns the word.
+template <bool PERWORD>
+__device__ __forceinline__ U4 draw(const Params &p, int w, uint32_t index, uint64_t g, uint32_t domain) {
+    if (PERWORD) {
+        const uint2 k = p.wkey[w];
+        return philox4x32_10(index, (uint32_t)g, domain, (uint32_t)(g >> 32), k.x, k.y);
+    }
+    return philox4x32_10(index, (uint32_t)g, domain, (uint32_t)(g >> 32), p.rk);
+}
+
+template <bool PERWORD>
+__device__ __forceinline__ uint64_t word_g0(const Params &p, int w) {
+    return PERWORD ? p.wg0[w] : p.g_base + 16ull * (uint64_t)w;
+}
+
+// IC: bits of `c` (trials of word w) whose edge e is live.  Coins come in
 // blocks of four trials, one Philox call per block that has a bit in c.
-__device__ __forceinline__ uint64_t ic_live_bits(uint32_t e, uint64_t g0, uint64_t c, uint32_t thr,
-                                                 const RoundKeys &rk, uint32_t &draws) {
+template <bool PERWORD>
+__device__ __forceinline__ uint64_t ic_live_bits(const Params &p, int w, uint32_t e, uint64_t c, uint32_t thr,
+                                                 uint32_t &draws) {
+    const uint64_t g0 = word_g0<PERWORD>(p, w);
     uint64_t live = 0;
     while (c) {
         ++draws;
         const int j = (__ffsll((long long)c) - 1) >> 2;
-        const uint64_t g = g0 + (uint64_t)j;
-        const U4 r = philox4x32_10(e, (uint32_t)g, 0u, (uint32_t)(g >> 32), rk);
+        const U4 r = draw<PERWORD>(p, w, e, g0 + (uint64_t)j, 0u);
         const uint32_t nib = (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
                              ((uint32_t)(r.w < thr) << 3);
         live |= (uint64_t)nib << (4 * j);
@@ -172,14 +191,34 @@ __device__ __forceinline__ void mark_dirty(const Params &p, int v, int w, uint64
 }
 
 // ---------------------------------------------------------------- seeds
-__global__ void k_seed_select(Params p, const int32_t *__restrict__ seeds, int32_t n_seeds, int32_t *__restrict__ bad) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_seeds; i += gridDim.x * blockDim.x) {
-        const int s = seeds[i];
-        if (s < 0 || s >= p.n) {
-            atomicExch(bad, 1);
-            continue;
+// A run of word columns of one item and the range of that item's seeds.
+struct SeedSeg {
+    int32_t s_begin, s_end;  // seeds[s_begin .. s_end)
+    int32_t col0, cnt;       // word columns [col0, col0 + cnt) of the pass
+};
+
+// Step 0: every seed is active in every valid trial of its item's words.  The
+// words go to nxt (dirty) and the seed to the list, so the seed step is then
+// finalized like an IC step.  Duplicate seeds write the same words.
+__global__ void k_seed(Params p, const SeedSeg *__restrict__ segs, int32_t n_segs, const int32_t *__restrict__ seeds,
+                       int32_t *__restrict__ bad) {
+    for (int j = blockIdx.x; j < n_segs; j += gridDim.x) {
+        const SeedSeg sg = segs[j];
+        for (int i = sg.s_begin + (int)threadIdx.x; i < sg.s_end; i += blockDim.x) {
+            const int s = seeds[i];
+            if (s < 0 || s >= p.n) {
+                atomicExch(bad, 1);
+                continue;
+            }
+            for (int w = sg.col0; w < sg.col0 + sg.cnt; ++w) {
+                const size_t idx = (size_t)s * p.B + w;
+                const uint64_t x = p.valid[w];
+                p.vis[idx] = x;
+                p.nxt[idx] = x;
+                atomicOr((unsigned long long *)(p.dmask + (size_t)s * p.nq + (w >> 6)), 1ull << (w & 63));
+            }
+            if (atomicExch(&p.mark[s], p.stamp) != p.stamp) p.lin[atomicAdd(p.lin_cnt, 1)] = s;
         }
-        if (atomicExch(&p.mark[s], p.stamp) != p.stamp) p.lin[atomicAdd(p.lin_cnt, 1)] = s;
     }
 }
 
@@ -206,8 +245,7 @@ constexpr int kNPB = kWarps * kNPW;     // nodes per block iteration
 // Block-cooperative finalize: each warp takes kNPW listed nodes per block
 // iteration, collects their words with frontier bits into slots, and emits
 // their work items.
-//   MODE 0 (seeds): every valid word, vis set to the valid mask.
-//   MODE 1 (IC):    the dirty words of nxt (new activations).
+//   MODE 1 (IC, and the seed step of both models): the dirty words of nxt.
 //   MODE 2 (LT):    rows touched for the first time in this pass are converted
 //                   (64 thresholds drawn once; acc = sum + ~theta; activation
 //                   where sum > theta); rows converted earlier carry the
@@ -216,7 +254,7 @@ constexpr int kNPB = kWarps * kNPW;     // nodes per block iteration
 // in nxt, still dirty, and its node is listed for the next step: expanding it
 // later, merged with later bits, leaves reachability (IC) and the least fixed
 // point (LT) unchanged.
-template <int MODE>
+template <int MODE, bool PERWORD>
 __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
     __shared__ int s_kept[kNPB], s_nch[kNPB], s_def[kNPB];
     __shared__ int s_off[kNPB], s_slot[kNPB], s_wb[kNPB], s_dpos[kNPB];
@@ -225,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
     const unsigned below = (1u << lane) - 1u;
     const int count = *p.lin_cnt;
     const int B = p.B, nq = p.nq;
-    const int tau = (MODE == 0 || p.force) ? 0 : p.tau;
+    const int tau = p.force ? 0 : p.tau;
     unsigned long long pc = 0;
     uint32_t n_dr = 0;
     for (int base = blockIdx.x * kNPB; base < count; base += gridDim.x * kNPB) {
@@ -239,10 +277,6 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
             KK[h] = 0;
             dm[h][0] = dm[h][1] = dm[h][2] = dm[h][3] = 0ull;
             if (!act) continue;
-            if (MODE == 0) {
-                KK[h] = p.nvalid;
-                continue;
-            }
             const uint64_t mine = (lane < nq) ? p.dmask[(size_t)vv[h] * nq + lane] : 0ull;
             if (lane < nq) p.dmask[(size_t)vv[h] * nq + lane] = 0ull;
 #pragma unroll
@@ -255,7 +289,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
         for (int h = 0; h < kNPW; ++h) {
             const int v = vv[h], K = KK[h];
             int kept = K, deferred = 0;
-            if (MODE != 0 && K > 0) {
+            if (K > 0) {
                 // the new bits of every listed word (LT: after the threshold test);
                 // words that wait go back into the dirty mask
                 kept = 0;
@@ -276,13 +310,11 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
                             } else {
                                 const uint64_t vis = p.vis[idx];
                                 uint4 *a4 = reinterpret_cast<uint4 *>(p.acc + idx * 64);
-                                const uint64_t g0 = p.g_base + 16ull * w;
+                                const uint64_t g0 = word_g0<PERWORD>(p, w);
 #pragma unroll 2
                                 for (int j = 0; j < 16; ++j) {
                                     ++n_dr;
-                                    const uint64_t g = g0 + (uint64_t)j;
-                                    const U4 th =
-                                        philox4x32_10((uint32_t)v, (uint32_t)g, 1u, (uint32_t)(g >> 32), p.rk);
+                                    const U4 th = draw<PERWORD>(p, w, (uint32_t)v, g0 + (uint64_t)j, 1u);
                                     uint4 s4 = a4[j];
                                     const uint64_t hit = (uint64_t)(s4.x > th.x) | ((uint64_t)(s4.y > th.y) << 1) |
                                                          ((uint64_t)(s4.z > th.z) << 2) |
@@ -380,17 +412,12 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
                 uint64_t x = 0;
                 int w = 0;
                 if (r < K) {
-                    w = MODE == 0 ? r : word_at(dm[h], r);
+                    w = word_at(dm[h], r);
                     const size_t idx = (size_t)v * B + w;
-                    if (MODE == 0) {
-                        x = p.valid[w];
-                        p.vis[idx] = x;
-                    } else {
-                        x = p.nxt[idx];
-                        // a word that waits got its dirty bit back in the pass above
-                        if (tau > 0 && ((p.dmask[(size_t)v * nq + (w >> 6)] >> (w & 63)) & 1ull)) x = 0ull;
-                        else p.nxt[idx] = 0ull;
-                    }
+                    x = p.nxt[idx];
+                    // a word that waits got its dirty bit back in the pass above
+                    if (tau > 0 && ((p.dmask[(size_t)v * nq + (w >> 6)] >> (w & 63)) & 1ull)) x = 0ull;
+                    else p.nxt[idx] = 0ull;
                     pc += __popcll(x);
                 }
                 const unsigned bm = __ballot_sync(kFull, x != 0ull);
@@ -413,7 +440,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
 // ---------------------------------------------------------------- push
 // One warp per work item: the item's (edge, pair) tasks are spread over the
 // lanes, task t = (edge t / k, pair t % k).
-template <int MODEL>
+template <int MODEL, bool PERWORD>
 __global__ void __launch_bounds__(kBlock) k_push(Params p) {
     __shared__ uint64_t s_b[kWarps][kMaxB];
     __shared__ uint16_t s_w[kWarps][kMaxB];
@@ -467,8 +494,7 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
                         const uint64_t c = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
                         if (c) {
                             uint64_t nb = c;
-                            if (thr != kAlways)
-                                nb &= ic_live_bits((uint32_t)e, p.g_base + 16ull * w, c, thr, p.rk, n_dr);
+                            if (thr != kAlways) nb &= ic_live_bits<PERWORD>(p, w, (uint32_t)e, c, thr, n_dr);
                             if (nb) {
                                 nb &= ~(uint64_t)atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)nb);
                                 if (nb) {
@@ -547,12 +573,16 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
 
 // ---------------------------------------------------------------- outputs
 // Per-trial spread: warp k of a block owns word w and reduces 32 nodes at a
-// time with one ballot per trial bit.
+// time with one ballot per trial bit; trial b of word w lands at
+// spread[wout[w] + b] (wout < 0: the word holds no trials).
 __global__ void __launch_bounds__(256) k_spread(const uint64_t *__restrict__ vis, int32_t n, int32_t B,
-                                                int32_t nwords, int32_t nodes_per_block, int32_t *__restrict__ spread) {
+                                                int32_t nwords, int32_t nodes_per_block,
+                                                const int64_t *__restrict__ wout, int32_t *__restrict__ spread) {
     const int lane = threadIdx.x & 31;
     const int w = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (w >= nwords) return;
+    const int64_t out = wout[w];
+    if (out < 0) return;
     const int v0 = blockIdx.y * nodes_per_block;
     const int v1 = min(n, v0 + nodes_per_block);
     uint32_t lo = 0, hi = 0;
@@ -570,26 +600,31 @@ __global__ void __launch_bounds__(256) k_spread(const uint64_t *__restrict__ vis
             }
         }
     }
-    if (lo) atomicAdd(&spread[w * 64 + lane], (int)lo);
-    if (hi) atomicAdd(&spread[w * 64 + 32 + lane], (int)hi);
+    if (lo) atomicAdd(&spread[out + lane], (int)lo);
+    if (hi) atomicAdd(&spread[out + 32 + lane], (int)hi);
 }
 
 // Per-node activation counts (accumulated over passes) and edge checks; one
-// warp per node, lanes over words.
+// warp per node, lanes over words.  witem == null: one count row; else the
+// count of word w goes to row witem[w] (one row per batch item).
 __global__ void __launch_bounds__(256) k_counts(const uint64_t *__restrict__ vis, int32_t n, int32_t B,
-                                                const int32_t *__restrict__ row_ptr, int32_t *__restrict__ count,
-                                                unsigned long long *__restrict__ checks) {
+                                                const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ witem,
+                                                int32_t *__restrict__ count, unsigned long long *__restrict__ checks) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int n_warps = (gridDim.x * blockDim.x) >> 5;
     unsigned long long ck = 0;
     for (int v = warp; v < n; v += n_warps) {
         int s = 0;
-        for (int w = lane; w < B; w += 32) s += __popcll(__ldcs((const unsigned long long *)vis + (size_t)v * B + w));
+        for (int w = lane; w < B; w += 32) {
+            const int c = __popcll(__ldcs((const unsigned long long *)vis + (size_t)v * B + w));
+            s += c;
+            if (witem && c && count) atomicAdd(&count[(size_t)witem[w] * n + v], c);
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
         if (lane == 0 && s) {
-            count[v] += s;
+            if (!witem && count) count[v] += s;
             ck += (unsigned long long)s * (unsigned long long)(row_ptr[v + 1] - row_ptr[v]);
         }
     }
@@ -653,88 +688,43 @@ static int blocks_for(int64_t warps, int max_blocks) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(b, max_blocks));
 }
 
-static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
-                           uint64_t rng_seed, int32_t *spread_out, int32_t *count_out, const cnd_sim_opts *opts) {
-    clear_error();
-    cnd_sim_opts o;
-    cnd_sim_opts_init(&o);
-    if (opts) o = *opts;
-    const char *fn = model == 0 ? "cnd_ic_simulate" : "cnd_lt_simulate";
-    if (!g) {
-        set_error("%s: graph is NULL", fn);
-        return CND_EINVAL;
-    }
-    const cnd_graph_dev &G = g->d;
-    const uint2 *edge = model == 0 ? G.ic_edge : G.lt_edge;
-    if (!edge && G.m > 0) {
-        set_error("%s: graph was created without %s", fn, model == 0 ? "IC probabilities" : "LT weights");
-        return CND_EINVAL;
-    }
-    if (n_seeds < 0 || (n_seeds > 0 && !seeds) || n_trials < 0 || n_trials > 0x7FFFFFFFll || o.first_trial < 0 ||
-        (o.first_trial & 63) || o.word_bits < 0 || (o.word_bits & 63) || o.word_bits > 64 * kMaxB ||
-        o.level_counts_len < 0 || (o.level_counts_len > 0 && !o.level_counts_out) || o.chunk_edges < 0 ||
-        o.direction < 0 || o.direction > 2 || o.defer_bits < 0 || o.defer_bits > 64) {
-        set_error("%s: bad arguments (n_seeds, n_trials, first_trial %% 64, word_bits, level_counts, chunk, defer_bits)",
-                  fn);
-        return CND_EINVAL;
-    }
-    if (o.defer_bits > 0 && (o.level_counts_len > 0 || o.max_levels > 0)) {
-        set_error("%s: defer_bits changes activation steps; it cannot be combined with level counts or max_levels", fn);
-        return CND_EINVAL;
-    }
-    const bool dev = o.device_ptrs != 0;
-    if (!dev) {
-        for (int32_t i = 0; i < n_seeds; ++i)
-            if (seeds[i] < 0 || seeds[i] >= G.n) {
-                set_error("%s: seed %d out of range", fn, seeds[i]);
-                return CND_EINVAL;
-            }
-    }
-    int prev_dev = 0;
-    CND_CUDA_TRY(cudaGetDevice(&prev_dev));
-    if (prev_dev != G.device) CND_CUDA_TRY(cudaSetDevice(G.device));
-    struct Restore {
-        int d, cur;
-        ~Restore() {
-            if (d != cur) cudaSetDevice(d);
-        }
-    } restore{prev_dev, G.device};
+// One simulation problem: a seed set, a trial count and a Philox key.
+struct ItemDesc {
+    int64_t seed_begin, seed_end;  // range in the seed array
+    int64_t trials;
+    int64_t out0;                  // position of its first trial in the spread output
+    uint64_t key;
+};
 
-    keep_pool(G.device);
-    Work W;
-    W.st = (cudaStream_t)o.stream;
+// Pass layout: runs of word columns, each from one item.
+struct Seg {
+    int32_t item;
+    int64_t lw0;  // first word of the item in this run
+    int32_t col0, cnt;
+};
+
+template <int MODEL, bool PERWORD>
+static const void *push_fn() {
+    return (const void *)k_push<MODEL, PERWORD>;
+}
+
+// Runs the items' trials: words of all items are packed into passes of B
+// word columns (an item may span passes; trials are independent), and each
+// pass runs the level loop over all its columns at once.
+//   seeds_dev: all seeds on the device; items index into it.
+//   spread: device, zeroed, sum of trials entries; counts: device, zeroed,
+//   n x (batched ? items : 1) entries, or null.
+static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, std::vector<ItemDesc> items,
+                            const int32_t *seeds_dev, bool batched, int32_t *d_spread, int32_t *d_count,
+                            unsigned long long *d_checks, unsigned long long *d_lc, int32_t *d_bad,
+                            const cnd_sim_opts &o, Work &W, bool &limit_hit) {
     cudaStream_t st = W.st;
     const int32_t n = G.n;
-
-    // ---- outputs on the device
-    const int64_t total_words = (n_trials + 63) / 64;
-    int32_t *d_spread = nullptr, *d_count = nullptr, *d_seeds = nullptr, *d_bad = nullptr;
-    unsigned long long *d_lc = nullptr, *d_checks = nullptr;
-    const int lc_len = o.level_counts_len;
-    CND_CUDA_TRY(W.alloc(&d_spread, (size_t)std::max<int64_t>(total_words, 1) * 64));
-    if (dev && count_out) d_count = count_out;
-    else CND_CUDA_TRY(W.alloc(&d_count, (size_t)n));
-    CND_CUDA_TRY(W.alloc(&d_lc, (size_t)std::max(lc_len, 1)));
-    CND_CUDA_TRY(W.alloc(&d_checks, 1));
-    CND_CUDA_TRY(W.alloc(&d_bad, 1));
-    if (dev) d_seeds = (int32_t *)seeds;
-    else {
-        CND_CUDA_TRY(W.alloc(&d_seeds, (size_t)std::max(n_seeds, 1)));
-        if (n_seeds) CND_CUDA_TRY(cudaMemcpyAsync(d_seeds, seeds, sizeof(int32_t) * n_seeds, cudaMemcpyHostToDevice, st));
-    }
-    CND_CUDA_TRY(cudaMemsetAsync(d_spread, 0, sizeof(int32_t) * (size_t)std::max<int64_t>(total_words, 1) * 64, st));
-    CND_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int32_t) * (size_t)n, st));
-    CND_CUDA_TRY(cudaMemsetAsync(d_lc, 0, sizeof(unsigned long long) * (size_t)std::max(lc_len, 1), st));
-    CND_CUDA_TRY(cudaMemsetAsync(d_checks, 0, sizeof(unsigned long long), st));
-    CND_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), st));
-
-    // ---- optional measurements
+    const uint2 *edge = model == 0 ? G.ic_edge : G.lt_edge;
+    int64_t total_words = 0;
+    for (const auto &it : items) total_words += (it.trials + 63) / 64;
     cnd_sim_stats *S = o.stats;
-    if (S) {
-        const int32_t flags = S->flags;
-        memset(S, 0, sizeof(*S));
-        S->flags = flags;
-    }
+    if (total_words == 0) return CND_OK;
     const bool timing = S && (S->flags & CND_STATS_TIMING);
     unsigned long long *d_ctr = nullptr;
     if (S && (S->flags & CND_STATS_COUNT)) {
@@ -751,7 +741,6 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
     if (timing)
         for (auto &x : ev.e) CND_CUDA_TRY(cudaEventCreate(&x));
     bool timing_pending = false;
-    int64_t launches = 0;
     auto collect_timing = [&]() -> cnd_status {
         if (!timing_pending) return CND_OK;
         float a = 0.f, b = 0.f;
@@ -763,206 +752,392 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         return CND_OK;
     };
 
-    bool limit_hit = false;
-    if (total_words > 0) {
-        // ---- pass width
-        size_t free_b = 0, total_b = 0;
-        CND_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-        const double budget = 0.6 * (double)free_b;
-        // bytes per word column: vis, nxt, two pair pools (+ LT accumulators)
-        const double per_word = (double)n * (2 * 8 + 2 * 10 + (model == 1 ? 256 : 0));
-        int64_t bmax = o.word_bits ? o.word_bits / 64 : kMaxB;
-        bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)(budget / per_word)));
-        bmax = std::min<int64_t>(bmax, kMaxB);
-        bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)0x7FFFFFFF / std::max(n, 1)));
-        const int64_t n_pass = (total_words + bmax - 1) / bmax;
-        const int B = (int)((total_words + n_pass - 1) / n_pass);
-        const int nq = (B + 63) / 64;
+    // ---- pass width
+    size_t free_b = 0, total_b = 0;
+    CND_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    const double budget = 0.6 * (double)free_b;
+    // bytes per word column: vis, nxt, two pair pools (+ LT accumulators)
+    const double per_word = (double)n * (2 * 8 + 2 * 10 + (model == 1 ? 256 : 0));
+    int64_t bmax = o.word_bits ? o.word_bits / 64 : kMaxB;
+    bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)(budget / per_word)));
+    bmax = std::min<int64_t>(bmax, kMaxB);
+    bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)0x7FFFFFFF / std::max(n, 1)));
+    const int64_t n_pass = (total_words + bmax - 1) / bmax;
+    const int B = (int)((total_words + n_pass - 1) / n_pass);
+    const int nq = (B + 63) / 64;
 
-        const size_t nB = (size_t)n * B;
-        const size_t work_cap = o.chunk_edges > 0
-                                    ? (size_t)n + (size_t)G.m / std::min(o.chunk_edges, 16384) + 1
-                                    : (size_t)n + 2 * (size_t)G.m * (size_t)B / kTasks + (size_t)G.m + 1;
-        Params P{};
-        P.n = n;
-        P.B = B;
-        P.nq = nq;
-        // (edge, pair) task indices of an item stay below 2^32 / k for the
-        // reciprocal division in k_push: at most 16384 edges x 256 pairs
-        P.chunk = std::min(o.chunk_edges, 16384);
-        P.row_ptr = G.row_ptr;
-        P.edge = edge;
-        P.rk = round_keys(rng_seed);
-        P.level_counts = d_lc;
-        P.lc_len = lc_len;
-        uint64_t *d_valid = nullptr;
-        Frontier fr[2];
-        CND_CUDA_TRY(W.alloc(&P.vis, nB));
-        CND_CUDA_TRY(W.alloc(&P.nxt, nB));
-        CND_CUDA_TRY(W.alloc(&P.dmask, (size_t)n * nq));
-        CND_CUDA_TRY(W.alloc(&P.mark, (size_t)n));
-        int32_t *lists[2] = {nullptr, nullptr}, *d_lcnt = nullptr;
-        CND_CUDA_TRY(W.alloc(&lists[0], (size_t)n));
-        CND_CUDA_TRY(W.alloc(&lists[1], (size_t)n));
-        CND_CUDA_TRY(W.alloc(&d_lcnt, 2));
-        CND_CUDA_TRY(W.alloc(&d_valid, (size_t)B));
-        P.tau = o.defer_bits;
-        P.max_wait = o.defer_steps;
-        if (o.defer_bits > 0 && o.defer_steps > 0) {
-            CND_CUDA_TRY(W.alloc(&P.age, nB));
-            CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
-        }
-        if (model == 1) {
-            CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
-            CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
-        }
-        for (int i = 0; i < 2; ++i) {
-            CND_CUDA_TRY(W.alloc(&fr[i].node, (size_t)n));
-            CND_CUDA_TRY(W.alloc(&fr[i].poff, (size_t)n));
-            CND_CUDA_TRY(W.alloc(&fr[i].pk, (size_t)n));
-            CND_CUDA_TRY(W.alloc(&fr[i].pw, nB));
-            CND_CUDA_TRY(W.alloc(&fr[i].pb, nB));
-            CND_CUDA_TRY(W.alloc(&fr[i].work, work_cap));
-            CND_CUDA_TRY(W.alloc(&fr[i].cnt, 4));
-        }
-        P.valid = d_valid;
-        P.ctr = d_ctr;
-        if (S) {
-            S->passes = (int32_t)n_pass;
-            S->word_bits = 64 * B;
-        }
-        CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
-        CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
-        CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
-        if (!t_pinned.h) CND_CUDA_TRY(cudaMallocHost(&t_pinned.h, 6 * sizeof(int32_t)));
-        if (o.defer_steps < 0 || o.defer_steps > 255) {
-            set_error("%s: defer_steps must be in 0..255", fn);
-            return CND_EINVAL;
-        }
-        int32_t *hcnt = t_pinned.h;
-
-        const void *k_push_fn = model == 0 ? (const void *)k_push<0> : (const void *)k_push<1>;
-        const void *k_fin_fn = model == 0 ? (const void *)k_finalize<1> : (const void *)k_finalize<2>;
-        const int push_blocks = G.num_sms * resident_blocks(k_push_fn);
-        const int fin_blocks = G.num_sms * resident_blocks(k_fin_fn);
-        const int seed_blocks = G.num_sms * resident_blocks((const void *)k_finalize<0>);
-        uint32_t stamp = 0;
-        std::vector<uint64_t> valid((size_t)B);
-        const auto t0 = std::chrono::steady_clock::now();
-
-        for (int64_t pass = 0; pass < n_pass; ++pass) {
-            const int64_t w0 = pass * B;
-            const int64_t nw_here = std::min<int64_t>(B, total_words - w0);
-            for (int w = 0; w < B; ++w) {
-                const int64_t word = w0 + w;
-                if (w >= nw_here) valid[w] = 0;
-                else {
-                    const int64_t left = n_trials - word * 64;
-                    valid[w] = left >= 64 ? ~0ull : ((1ull << left) - 1ull);
+    // ---- pass layout: items by decreasing size, runs of columns
+    std::vector<int32_t> order(items.size());
+    for (size_t i = 0; i < items.size(); ++i) order[i] = (int32_t)i;
+    if (batched)
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t b) { return items[a].trials > items[b].trials; });
+    std::vector<std::vector<Seg>> passes(1);
+    {
+        int32_t col = 0;
+        for (int32_t it : order) {
+            int64_t words = (items[it].trials + 63) / 64, lw = 0;
+            while (words > 0) {
+                if (col == B) {
+                    passes.emplace_back();
+                    col = 0;
                 }
-            }
-            P.nvalid = (int32_t)nw_here;
-            CND_CUDA_TRY(cudaMemcpyAsync(d_valid, valid.data(), sizeof(uint64_t) * B, cudaMemcpyHostToDevice, st));
-            CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
-            if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
-            if (model == 1) {
-                CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
-                CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, st));
-            }
-            P.g_base = (uint64_t)(o.first_trial + 64 * w0) >> 2;
-
-            // step 0: seeds (finalized from list 1; nothing waits afterwards)
-            int cur = 0;
-            CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 4 * sizeof(int32_t), st));
-            CND_CUDA_TRY(cudaMemsetAsync(d_lcnt, 0, 2 * sizeof(int32_t), st));
-            P.out = fr[cur];
-            P.lin = lists[1];
-            P.lin_cnt = d_lcnt + 1;
-            P.lnext = lists[0];
-            P.lnext_cnt = d_lcnt;
-            P.force = 0;
-            P.stamp = stamp++;
-            P.level = 0;
-            if (n_seeds > 0) {
-                k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, G.num_sms * 8)), 256, 0, st>>>(
-                    P, d_seeds, n_seeds, d_bad);
-                CND_CUDA_TRY(cudaGetLastError());
-                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for((n_seeds + kNPW - 1) / kNPW, seed_blocks), st, P));
-                launches += 2;
-            }
-            for (int L = 0;; ++L) {
-                CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                CND_CUDA_TRY(cudaMemcpyAsync(hcnt + 4, d_lcnt + (L & 1), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-                CND_CUDA_TRY(cudaStreamSynchronize(st));
-                if (timing) {
-                    const cnd_status ts = collect_timing();
-                    if (ts != CND_OK) return ts;
-                }
-                // slots / work items of step L's frontier; nodes whose words wait
-                const int32_t slots = hcnt[1], items = hcnt[2], waiting = hcnt[4];
-                if (S) {
-                    S->frontier_slots += slots;
-                    S->work_items += items;
-                }
-                if (slots == 0 && waiting == 0) break;
-                if (o.max_levels > 0 && L >= o.max_levels) {
-                    limit_hit = true;
-                    break;
-                }
-                if (items == 0 && waiting == 0) break;
-                if (o.timeout_s > 0) {
-                    const double el =
-                        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-                    if (el > o.timeout_s) {
-                        set_error("%s: timed out after %.3f s", fn, el);
-                        cudaStreamSynchronize(st);
-                        return CND_ETIMEOUT;
-                    }
-                }
-                const int nx = cur ^ 1;
-                CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
-                CND_CUDA_TRY(cudaMemsetAsync(d_lcnt + ((L + 1) & 1), 0, sizeof(int32_t), st));
-                P.in = fr[cur];
-                P.out = fr[nx];
-                P.lin = lists[L & 1];
-                P.lin_cnt = d_lcnt + (L & 1);
-                P.lnext = lists[(L + 1) & 1];
-                P.lnext_cnt = d_lcnt + ((L + 1) & 1);
-                P.stamp = stamp++;
-                P.level = L + 1;
-                // nothing to expand in this step: every waiting word goes now
-                P.force = items == 0 ? 1 : 0;
-                if (timing) CND_CUDA_TRY(cudaEventRecord(ev.e[0], st));
-                if (items > 0) CND_CUDA_TRY(launch(k_push_fn, blocks_for(items, push_blocks), st, P));
-                if (timing) {
-                    CND_CUDA_TRY(cudaEventRecord(ev.e[1], st));
-                    CND_CUDA_TRY(cudaEventRecord(ev.e[2], st));
-                }
-                CND_CUDA_TRY(launch(k_fin_fn, fin_blocks, st, P));
-                if (timing) {
-                    CND_CUDA_TRY(cudaEventRecord(ev.e[3], st));
-                    timing_pending = true;
-                }
-                launches += 2;
-                if (S) {
-                    S->levels += 1;
-                    S->expand_launches += 1;
-                    S->finalize_launches += 1;
-                }
-                cur = nx;
-            }
-            // outputs of this pass
-            {
-                const int npb = 4096;
-                dim3 grid((unsigned)((nw_here + 7) / 8), (unsigned)((n + npb - 1) / npb));
-                k_spread<<<grid, 256, 0, st>>>(P.vis, n, B, (int)nw_here, npb, d_spread + w0 * 64);
-                CND_CUDA_TRY(cudaGetLastError());
-                k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, st>>>(P.vis, n, B, G.row_ptr, d_count, d_checks);
-                CND_CUDA_TRY(cudaGetLastError());
-                launches += 2;
+                const int32_t take = (int32_t)std::min<int64_t>(words, B - col);
+                passes.back().push_back(Seg{it, lw, col, take});
+                col += take;
+                lw += take;
+                words -= take;
             }
         }
     }
+
+    const size_t nB = (size_t)n * B;
+    const int chunk = std::min(o.chunk_edges, 16384);  // task index < 2^32 / k in k_push's division
+    const size_t work_cap = chunk > 0 ? (size_t)n + (size_t)G.m / chunk + 1
+                                      : (size_t)n + 2 * (size_t)G.m * (size_t)B / kTasks + (size_t)G.m + 1;
+    Params P{};
+    P.n = n;
+    P.B = B;
+    P.nq = nq;
+    P.chunk = chunk;
+    P.row_ptr = G.row_ptr;
+    P.edge = edge;
+    P.rk = round_keys(items[0].key);
+    P.level_counts = d_lc;
+    P.lc_len = o.level_counts_len;
+    Frontier fr[2];
+    CND_CUDA_TRY(W.alloc(&P.vis, nB));
+    CND_CUDA_TRY(W.alloc(&P.nxt, nB));
+    CND_CUDA_TRY(W.alloc(&P.dmask, (size_t)n * nq));
+    CND_CUDA_TRY(W.alloc(&P.mark, (size_t)n));
+    int32_t *lists[2] = {nullptr, nullptr}, *d_lcnt = nullptr;
+    CND_CUDA_TRY(W.alloc(&lists[0], (size_t)n));
+    CND_CUDA_TRY(W.alloc(&lists[1], (size_t)n));
+    CND_CUDA_TRY(W.alloc(&d_lcnt, 2));
+    // per-pass column descriptors, uploaded as one block:
+    // valid[B] | wg0[B] | wout[B] | wkey[B] | witem[B] (+pad) | seed runs
+    size_t max_runs = 0;
+    for (const auto &ps : passes) max_runs = std::max(max_runs, ps.size());
+    const size_t desc_words = 4 * (size_t)B + (size_t)(B + 1) / 2 + 2 * max_runs;
+    uint64_t *d_desc = nullptr;
+    CND_CUDA_TRY(W.alloc(&d_desc, desc_words));
+    std::vector<uint64_t> h_desc(desc_words, 0);
+    uint64_t *h_valid = h_desc.data(), *h_wg0 = h_valid + B;
+    int64_t *h_wout = (int64_t *)(h_wg0 + B);
+    uint2 *h_wkey = (uint2 *)(h_wout + B);
+    int32_t *h_witem = (int32_t *)(h_wkey + B);
+    SeedSeg *h_segs = (SeedSeg *)(h_desc.data() + 4 * (size_t)B + (size_t)(B + 1) / 2);
+    P.valid = d_desc;
+    P.wg0 = d_desc + B;
+    const int64_t *d_wout = (const int64_t *)(d_desc + 2 * (size_t)B);
+    P.wkey = (const uint2 *)(d_desc + 3 * (size_t)B);
+    const int32_t *d_witem = (const int32_t *)(d_desc + 4 * (size_t)B);
+    const SeedSeg *d_segs = (const SeedSeg *)(d_desc + 4 * (size_t)B + (size_t)(B + 1) / 2);
+
+    P.tau = o.defer_bits;
+    P.max_wait = o.defer_steps;
+    if (o.defer_bits > 0 && o.defer_steps > 0) CND_CUDA_TRY(W.alloc(&P.age, nB));
+    if (model == 1) {
+        CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
+        CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
+    }
+    for (int i = 0; i < 2; ++i) {
+        CND_CUDA_TRY(W.alloc(&fr[i].node, (size_t)n));
+        CND_CUDA_TRY(W.alloc(&fr[i].poff, (size_t)n));
+        CND_CUDA_TRY(W.alloc(&fr[i].pk, (size_t)n));
+        CND_CUDA_TRY(W.alloc(&fr[i].pw, nB));
+        CND_CUDA_TRY(W.alloc(&fr[i].pb, nB));
+        CND_CUDA_TRY(W.alloc(&fr[i].work, work_cap));
+        CND_CUDA_TRY(W.alloc(&fr[i].cnt, 4));
+    }
+    P.ctr = d_ctr;
+    if (S) {
+        S->passes = (int32_t)passes.size();
+        S->word_bits = 64 * B;
+    }
+    CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
+    CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
+    CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
+    if (!t_pinned.h) CND_CUDA_TRY(cudaMallocHost(&t_pinned.h, 6 * sizeof(int32_t)));
+    int32_t *hcnt = t_pinned.h;
+
+    // a pass whose columns share one key takes it as launch parameters
+    const void *k_push_pw = model == 0 ? push_fn<0, true>() : push_fn<1, true>();
+    const void *k_push_uk = model == 0 ? push_fn<0, false>() : push_fn<1, false>();
+    const void *k_fin_pw = model == 0 ? (const void *)k_finalize<1, true> : (const void *)k_finalize<2, true>;
+    const void *k_fin_uk = model == 0 ? (const void *)k_finalize<1, false> : (const void *)k_finalize<2, false>;
+    const void *k_seedfin = (const void *)k_finalize<1, false>;
+    const int push_blocks = G.num_sms * resident_blocks(k_push_uk);
+    const int fin_blocks = G.num_sms * resident_blocks(k_fin_uk);
+    const int seed_blocks = G.num_sms * resident_blocks(k_seedfin);
+    uint32_t stamp = 0;
+    int64_t launches = 0;
+    const auto t0 = std::chrono::steady_clock::now();
+
+    for (size_t pass = 0; pass < passes.size(); ++pass) {
+        const std::vector<Seg> &ps = passes[pass];
+        std::fill(h_desc.begin(), h_desc.end(), 0ull);
+        bool one_key = true;
+        int32_t nw_here = 0;
+        for (size_t r = 0; r < ps.size(); ++r) {
+            const Seg &sg = ps[r];
+            const ItemDesc &it = items[sg.item];
+            one_key = one_key && it.key == items[ps[0].item].key;
+            for (int32_t c = 0; c < sg.cnt; ++c) {
+                const int32_t col = sg.col0 + c;
+                const int64_t lw = sg.lw0 + c;
+                const int64_t left = it.trials - 64 * lw;
+                h_valid[col] = left >= 64 ? ~0ull : ((1ull << left) - 1ull);
+                h_wg0[col] = (uint64_t)(o.first_trial + 64 * lw) >> 2;
+                h_wout[col] = it.out0 + 64 * lw;
+                h_wkey[col] = make_uint2((uint32_t)it.key, (uint32_t)(it.key >> 32));
+                h_witem[col] = sg.item;
+            }
+            h_segs[r] = SeedSeg{(int32_t)it.seed_begin, (int32_t)it.seed_end, sg.col0, sg.cnt};
+            nw_here = std::max(nw_here, sg.col0 + sg.cnt);
+        }
+        for (int32_t col = nw_here; col < B; ++col) h_wout[col] = -1;
+        // one key and consecutive trial blocks: the key goes in the launch parameters
+        bool uniform = one_key;
+        for (int32_t col = 1; col < nw_here && uniform; ++col) uniform = h_wg0[col] == h_wg0[0] + 16ull * col;
+        const bool pw = !uniform;
+        P.rk = round_keys(items[ps[0].item].key);
+        P.g_base = h_wg0[0];
+        P.nvalid = nw_here;
+        CND_CUDA_TRY(
+            cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(uint64_t) * desc_words, cudaMemcpyHostToDevice, st));
+        CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
+        if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
+        if (model == 1) {
+            CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
+            CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, st));
+        }
+        const void *k_push_fn = pw ? k_push_pw : k_push_uk;
+        const void *k_fin_fn = pw ? k_fin_pw : k_fin_uk;
+
+        // step 0: seeds (finalized from list 1 like an IC step; nothing waits)
+        int cur = 0;
+        CND_CUDA_TRY(cudaMemsetAsync(fr[cur].cnt, 0, 4 * sizeof(int32_t), st));
+        CND_CUDA_TRY(cudaMemsetAsync(d_lcnt, 0, 2 * sizeof(int32_t), st));
+        P.out = fr[cur];
+        P.lin = lists[1];
+        P.lin_cnt = d_lcnt + 1;
+        P.lnext = lists[0];
+        P.lnext_cnt = d_lcnt;
+        P.force = 1;
+        P.stamp = stamp++;
+        P.level = 0;
+        k_seed<<<std::max<int>(1, (int)ps.size()), 128, 0, st>>>(P, d_segs, (int32_t)ps.size(), seeds_dev, d_bad);
+        CND_CUDA_TRY(cudaGetLastError());
+        CND_CUDA_TRY(launch(k_seedfin, seed_blocks, st, P));
+        launches += 2;
+        P.force = 0;
+        for (int L = 0;; ++L) {
+            CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CND_CUDA_TRY(cudaMemcpyAsync(hcnt + 4, d_lcnt + (L & 1), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CND_CUDA_TRY(cudaStreamSynchronize(st));
+            if (timing) {
+                const cnd_status ts = collect_timing();
+                if (ts != CND_OK) return ts;
+            }
+            // slots / work items of step L's frontier; nodes whose words wait
+            const int32_t slots = hcnt[1], n_items_w = hcnt[2], waiting = hcnt[4];
+            if (S) {
+                S->frontier_slots += slots;
+                S->work_items += n_items_w;
+            }
+            if (slots == 0 && waiting == 0) break;
+            if (o.max_levels > 0 && L >= o.max_levels) {
+                limit_hit = true;
+                break;
+            }
+            if (n_items_w == 0 && waiting == 0) break;
+            if (o.timeout_s > 0) {
+                const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                if (el > o.timeout_s) {
+                    set_error("%s: timed out after %.3f s", fn, el);
+                    cudaStreamSynchronize(st);
+                    return CND_ETIMEOUT;
+                }
+            }
+            const int nx = cur ^ 1;
+            CND_CUDA_TRY(cudaMemsetAsync(fr[nx].cnt, 0, 4 * sizeof(int32_t), st));
+            CND_CUDA_TRY(cudaMemsetAsync(d_lcnt + ((L + 1) & 1), 0, sizeof(int32_t), st));
+            P.in = fr[cur];
+            P.out = fr[nx];
+            P.lin = lists[L & 1];
+            P.lin_cnt = d_lcnt + (L & 1);
+            P.lnext = lists[(L + 1) & 1];
+            P.lnext_cnt = d_lcnt + ((L + 1) & 1);
+            P.stamp = stamp++;
+            P.level = L + 1;
+            // nothing to expand in this step: every waiting word goes now
+            P.force = n_items_w == 0 ? 1 : 0;
+            if (timing) CND_CUDA_TRY(cudaEventRecord(ev.e[0], st));
+            if (n_items_w > 0) {
+                CND_CUDA_TRY(launch(k_push_fn, blocks_for(n_items_w, push_blocks), st, P));
+                launches += 1;
+            }
+            if (timing) {
+                CND_CUDA_TRY(cudaEventRecord(ev.e[1], st));
+                CND_CUDA_TRY(cudaEventRecord(ev.e[2], st));
+            }
+            CND_CUDA_TRY(launch(k_fin_fn, fin_blocks, st, P));
+            if (timing) {
+                CND_CUDA_TRY(cudaEventRecord(ev.e[3], st));
+                timing_pending = true;
+            }
+            launches += 1;
+            if (S) {
+                S->levels += 1;
+                S->expand_launches += n_items_w > 0 ? 1 : 0;
+                S->finalize_launches += 1;
+            }
+            cur = nx;
+        }
+        // outputs of this pass
+        const int npb = 4096;
+        dim3 grid((unsigned)((nw_here + 7) / 8), (unsigned)((n + npb - 1) / npb));
+        k_spread<<<grid, 256, 0, st>>>(P.vis, n, B, nw_here, npb, d_wout, d_spread);
+        CND_CUDA_TRY(cudaGetLastError());
+        k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, st>>>(P.vis, n, B, G.row_ptr, batched ? d_witem : nullptr,
+                                                                d_count, d_checks);
+        CND_CUDA_TRY(cudaGetLastError());
+        launches += 2;
+    }
+    if (S) S->launches = launches;
+    if (d_ctr) {
+        unsigned long long hctr[C_N] = {0, 0, 0, 0, 0};
+        CND_CUDA_TRY(cudaMemcpyAsync(hctr, d_ctr, sizeof(hctr), cudaMemcpyDeviceToHost, st));
+        CND_CUDA_TRY(cudaStreamSynchronize(st));
+        S->edges_scanned = (int64_t)hctr[C_EDGES];
+        S->frontier_words = (int64_t)hctr[C_FWORDS];
+        S->word_checks = (int64_t)hctr[C_WCHECKS];
+        S->draws = (int64_t)hctr[C_DRAWS];
+        S->updates = (int64_t)hctr[C_UPDATES];
+    }
+    CND_CUDA_TRY(cudaStreamSynchronize(st));
+    if (timing) return collect_timing();
+    return CND_OK;
+}
+
+// Shared front end of the single and batched entry points.
+static cnd_status simulate_common(int model, const cnd_graph *g, const char *fn, int32_t n_items,
+                                  const int64_t *seed_off, const int32_t *seeds, const int32_t *n_trials_arr,
+                                  int64_t n_trials_one, const uint64_t *keys, uint64_t key_one, int32_t *spread_out,
+                                  int32_t *count_out, const cnd_sim_opts *opts) {
+    clear_error();
+    cnd_sim_opts o;
+    cnd_sim_opts_init(&o);
+    if (opts) o = *opts;
+    const bool batched = n_trials_arr != nullptr;
+    if (!g) {
+        set_error("%s: graph is NULL", fn);
+        return CND_EINVAL;
+    }
+    const cnd_graph_dev &G = g->d;
+    const uint2 *edge = model == 0 ? G.ic_edge : G.lt_edge;
+    if (!edge && G.m > 0) {
+        set_error("%s: graph was created without %s", fn, model == 0 ? "IC probabilities" : "LT weights");
+        return CND_EINVAL;
+    }
+    if (n_items < 0 || (batched && n_items > 0 && (!seed_off || !keys)) || o.first_trial < 0 ||
+        (o.first_trial & 63) || o.word_bits < 0 || (o.word_bits & 63) || o.word_bits > 64 * kMaxB ||
+        o.level_counts_len < 0 || (o.level_counts_len > 0 && !o.level_counts_out) || o.chunk_edges < 0 ||
+        o.direction < 0 || o.direction > 2 || o.defer_bits < 0 || o.defer_bits > 64 || o.defer_steps < 0 ||
+        o.defer_steps > 255) {
+        set_error("%s: bad arguments (items, first_trial %% 64, word_bits, level_counts, chunk, defer)", fn);
+        return CND_EINVAL;
+    }
+    if (o.defer_bits > 0 && (o.level_counts_len > 0 || o.max_levels > 0)) {
+        set_error("%s: defer_bits changes activation steps; it cannot be combined with level counts or max_levels", fn);
+        return CND_EINVAL;
+    }
+    // ---- items
+    std::vector<ItemDesc> items((size_t)n_items);
+    int64_t total_trials = 0, n_seeds_total = 0;
+    for (int32_t i = 0; i < n_items; ++i) {
+        ItemDesc &it = items[i];
+        it.seed_begin = batched ? seed_off[i] : 0;
+        it.seed_end = batched ? seed_off[i + 1] : seed_off[1];
+        it.trials = batched ? n_trials_arr[i] : n_trials_one;
+        it.key = batched ? keys[i] : key_one;
+        it.out0 = total_trials;
+        if (it.seed_begin < 0 || it.seed_end < it.seed_begin || it.seed_end > 0x7FFFFFFFll || it.trials < 0 ||
+            it.trials > 0x7FFFFFFFll) {
+            set_error("%s: item %d: bad seed range or trial count", fn, i);
+            return CND_EINVAL;
+        }
+        total_trials += it.trials;
+        n_seeds_total = std::max(n_seeds_total, it.seed_end);
+    }
+    if (n_seeds_total > 0 && !seeds) {
+        set_error("%s: seeds is NULL", fn);
+        return CND_EINVAL;
+    }
+    const bool dev = o.device_ptrs != 0;
+    if (!dev)
+        for (int64_t i = 0; i < n_seeds_total; ++i)
+            if (seeds[i] < 0 || seeds[i] >= G.n) {
+                set_error("%s: seed %d out of range", fn, seeds[i]);
+                return CND_EINVAL;
+            }
+    int prev_dev = 0;
+    CND_CUDA_TRY(cudaGetDevice(&prev_dev));
+    if (prev_dev != G.device) CND_CUDA_TRY(cudaSetDevice(G.device));
+    struct Restore {
+        int d, cur;
+        ~Restore() {
+            if (d != cur) cudaSetDevice(d);
+        }
+    } restore{prev_dev, G.device};
+
+    keep_pool(G.device);
+    Work W;
+    W.st = (cudaStream_t)o.stream;
+    cudaStream_t st = W.st;
+    const int32_t n = G.n;
+    const size_t count_rows = batched ? (size_t)n_items : 1;
+
+    // ---- outputs on the device
+    int32_t *d_spread = nullptr, *d_count = nullptr, *d_bad = nullptr;
+    const int32_t *d_seeds = nullptr;
+    unsigned long long *d_lc = nullptr, *d_checks = nullptr;
+    const int lc_len = o.level_counts_len;
+    if (dev && spread_out) d_spread = spread_out;
+    else CND_CUDA_TRY(W.alloc(&d_spread, (size_t)std::max<int64_t>(total_trials, 1)));
+    if (count_out) {
+        if (dev) d_count = count_out;
+        else CND_CUDA_TRY(W.alloc(&d_count, (size_t)n * count_rows));
+    }
+    CND_CUDA_TRY(W.alloc(&d_lc, (size_t)std::max(lc_len, 1)));
+    CND_CUDA_TRY(W.alloc(&d_checks, 1));
+    CND_CUDA_TRY(W.alloc(&d_bad, 1));
+    if (dev) {
+        d_seeds = seeds;
+    } else {
+        int32_t *tmp = nullptr;
+        CND_CUDA_TRY(W.alloc(&tmp, (size_t)std::max<int64_t>(n_seeds_total, 1)));
+        if (n_seeds_total)
+            CND_CUDA_TRY(cudaMemcpyAsync(tmp, seeds, sizeof(int32_t) * n_seeds_total, cudaMemcpyHostToDevice, st));
+        d_seeds = tmp;
+    }
+    if (total_trials) CND_CUDA_TRY(cudaMemsetAsync(d_spread, 0, sizeof(int32_t) * (size_t)total_trials, st));
+    if (d_count) CND_CUDA_TRY(cudaMemsetAsync(d_count, 0, sizeof(int32_t) * (size_t)n * count_rows, st));
+    CND_CUDA_TRY(cudaMemsetAsync(d_lc, 0, sizeof(unsigned long long) * (size_t)std::max(lc_len, 1), st));
+    CND_CUDA_TRY(cudaMemsetAsync(d_checks, 0, sizeof(unsigned long long), st));
+    CND_CUDA_TRY(cudaMemsetAsync(d_bad, 0, sizeof(int32_t), st));
+
+    cnd_sim_stats *S = o.stats;
+    if (S) {
+        const int32_t flags = S->flags;
+        memset(S, 0, sizeof(*S));
+        S->flags = flags;
+    }
+    bool limit_hit = false;
+    const cnd_status rs =
+        run_items(model, G, fn, items, d_seeds, batched, d_spread, d_count, d_checks, d_lc, d_bad, o, W, limit_hit);
+    if (rs != CND_OK) return rs;
 
     // ---- results
     int32_t hbad = 0;
@@ -970,35 +1145,21 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
     std::vector<unsigned long long> hlc((size_t)std::max(lc_len, 1));
     unsigned long long hchecks = 0;
     if (dev) {
-        if (spread_out && n_trials)
-            CND_CUDA_TRY(cudaMemcpyAsync(spread_out, d_spread, sizeof(int32_t) * n_trials, cudaMemcpyDeviceToDevice, st));
         if (o.edge_checks_out)
             CND_CUDA_TRY(cudaMemcpyAsync(o.edge_checks_out, d_checks, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
         if (lc_len)
             CND_CUDA_TRY(cudaMemcpyAsync(o.level_counts_out, d_lc, sizeof(int64_t) * lc_len, cudaMemcpyDeviceToDevice, st));
     } else {
-        if (spread_out && n_trials)
-            CND_CUDA_TRY(cudaMemcpyAsync(spread_out, d_spread, sizeof(int32_t) * n_trials, cudaMemcpyDeviceToHost, st));
-        if (count_out) CND_CUDA_TRY(cudaMemcpyAsync(count_out, d_count, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, st));
+        if (spread_out && total_trials)
+            CND_CUDA_TRY(cudaMemcpyAsync(spread_out, d_spread, sizeof(int32_t) * total_trials, cudaMemcpyDeviceToHost, st));
+        if (count_out)
+            CND_CUDA_TRY(cudaMemcpyAsync(count_out, d_count, sizeof(int32_t) * (size_t)n * count_rows,
+                                         cudaMemcpyDeviceToHost, st));
         CND_CUDA_TRY(cudaMemcpyAsync(&hchecks, d_checks, sizeof(hchecks), cudaMemcpyDeviceToHost, st));
         if (lc_len)
             CND_CUDA_TRY(cudaMemcpyAsync(hlc.data(), d_lc, sizeof(unsigned long long) * lc_len, cudaMemcpyDeviceToHost, st));
     }
-    unsigned long long hctr[C_N] = {0, 0, 0, 0, 0};
-    if (d_ctr) CND_CUDA_TRY(cudaMemcpyAsync(hctr, d_ctr, sizeof(hctr), cudaMemcpyDeviceToHost, st));
     CND_CUDA_TRY(cudaStreamSynchronize(st));
-    if (timing) {
-        const cnd_status ts = collect_timing();
-        if (ts != CND_OK) return ts;
-    }
-    if (S) {
-        S->launches = launches;
-        S->edges_scanned = (int64_t)hctr[C_EDGES];
-        S->frontier_words = (int64_t)hctr[C_FWORDS];
-        S->word_checks = (int64_t)hctr[C_WCHECKS];
-        S->draws = (int64_t)hctr[C_DRAWS];
-        S->updates = (int64_t)hctr[C_UPDATES];
-    }
     if (!dev) {
         if (o.edge_checks_out) *o.edge_checks_out = (int64_t)hchecks;
         for (int i = 0; i < lc_len; ++i) o.level_counts_out[i] = (int64_t)hlc[i];
@@ -1012,6 +1173,36 @@ static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, 
         return CND_ELIMIT;
     }
     return CND_OK;
+}
+
+static cnd_status simulate(int model, const cnd_graph *g, const int32_t *seeds, int32_t n_seeds, int64_t n_trials,
+                           uint64_t rng_seed, int32_t *spread_out, int32_t *count_out, const cnd_sim_opts *opts) {
+    const char *fn = model == 0 ? "cnd_ic_simulate" : "cnd_lt_simulate";
+    if (n_seeds < 0 || (n_seeds > 0 && !seeds) || n_trials < 0 || n_trials > 0x7FFFFFFFll) {
+        clear_error();
+        set_error("%s: bad arguments (n_seeds, seeds, n_trials)", fn);
+        return CND_EINVAL;
+    }
+    const int64_t off[2] = {0, n_seeds};
+    return simulate_common(model, g, fn, 1, off, seeds, nullptr, n_trials, nullptr, rng_seed, spread_out, count_out,
+                           opts);
+}
+
+static cnd_status simulate_batch(int model, const cnd_graph *g, int32_t n_items, const int64_t *seed_off,
+                                 const int32_t *seeds, const int32_t *n_trials, const uint64_t *rng_seed,
+                                 int32_t *spread_out, int32_t *count_out, const cnd_sim_opts *opts) {
+    const char *fn = model == 0 ? "cnd_ic_simulate_batch" : "cnd_lt_simulate_batch";
+    if (n_items < 0 || (n_items > 0 && (!seed_off || !n_trials || !rng_seed))) {
+        clear_error();
+        set_error("%s: bad arguments (n_items, seed_off, n_trials, rng_seed)", fn);
+        return CND_EINVAL;
+    }
+    if (n_items == 0) {
+        clear_error();
+        return CND_OK;
+    }
+    return simulate_common(model, g, fn, n_items, seed_off, seeds, n_trials, 0, rng_seed, 0, spread_out, count_out,
+                           opts);
 }
 
 }  // namespace cnd
@@ -1040,6 +1231,18 @@ cnd_status cnd_lt_simulate_ex(const cnd_graph *g, const int32_t *seeds, int32_t 
                               uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out,
                               const cnd_sim_opts *opts) {
     return simulate(1, g, seeds, n_seeds, n_trials, rng_seed, spread_out, node_count_out, opts);
+}
+
+cnd_status cnd_ic_simulate_batch(const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,
+                                 const int32_t *n_trials, const uint64_t *rng_seed, int32_t *spread_out,
+                                 int32_t *node_count_out, const cnd_sim_opts *opts) {
+    return simulate_batch(0, g, n_items, seed_off, seeds, n_trials, rng_seed, spread_out, node_count_out, opts);
+}
+
+cnd_status cnd_lt_simulate_batch(const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,
+                                 const int32_t *n_trials, const uint64_t *rng_seed, int32_t *spread_out,
+                                 int32_t *node_count_out, const cnd_sim_opts *opts) {
+    return simulate_batch(1, g, n_items, seed_off, seeds, n_trials, rng_seed, spread_out, node_count_out, opts);
 }
 
 }  // extern "C"
@@ -1114,7 +1317,7 @@ static size_t place_static(Arena &a, Params &P, Frontier (&fr)[2], int32_t n, in
     P.lnext = a.take<int32_t>((size_t)n);
     P.lin_cnt = a.take<int32_t>(2);
     P.lnext_cnt = P.lin_cnt ? P.lin_cnt + 1 : nullptr;
-    *d_valid = a.take<uint64_t>((size_t)B);
+    *d_valid = a.take<uint64_t>(2 * (size_t)B + 2);  // valid[B] | wout[B] | one seed run
     *d_checks = a.take<unsigned long long>(1);
     *d_bad = a.take<int32_t>(1);
     for (int i = 0; i < 2; ++i) {
@@ -1205,10 +1408,15 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
         CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
         CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
         CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
-        const int push_blocks = G.num_sms * resident_blocks((const void *)k_push<0>);
-        const int fin_blocks = G.num_sms * resident_blocks((const void *)k_finalize<1>);
-        const int seed_blocks = G.num_sms * resident_blocks((const void *)k_finalize<0>);
-        uint64_t valid[kMaxB];
+        const void *k_push_fn = (const void *)k_push<0, false>;
+        const void *k_fin_fn = (const void *)k_finalize<1, false>;
+        const int push_blocks = G.num_sms * resident_blocks(k_push_fn);
+        const int fin_blocks = G.num_sms * resident_blocks(k_fin_fn);
+        uint64_t desc[2 * kMaxB + 2];  // valid[B] | wout[B] | one seed run
+        uint64_t *valid = desc;
+        int64_t *wout = (int64_t *)(desc + B);
+        const int64_t *d_wout = (const int64_t *)(d_valid + B);
+        const SeedSeg *d_seg = (const SeedSeg *)(d_valid + 2 * B);
         int32_t hcnt[4];
         uint32_t stamp = 0;
         for (int64_t pass = 0; pass < n_pass; ++pass) {
@@ -1217,9 +1425,11 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
             for (int w = 0; w < B; ++w) {
                 const int64_t left = n_trials - (w0 + w) * 64;
                 valid[w] = w >= nw_here ? 0ull : (left >= 64 ? ~0ull : ((1ull << left) - 1ull));
+                wout[w] = w >= nw_here ? -1 : 64 * (w0 + w);
             }
+            *(SeedSeg *)(desc + 2 * B) = SeedSeg{0, n_seeds, 0, (int32_t)nw_here};
             P.nvalid = (int32_t)nw_here;
-            CND_CUDA_TRY(cudaMemcpyAsync(d_valid, valid, sizeof(uint64_t) * B, cudaMemcpyHostToDevice, st));
+            CND_CUDA_TRY(cudaMemcpyAsync(d_valid, desc, sizeof(uint64_t) * (2 * B + 2), cudaMemcpyHostToDevice, st));
             CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
             P.g_base = (uint64_t)(64 * w0) >> 2;
             int cur = 0;
@@ -1228,12 +1438,11 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
             P.out = fr[cur];
             P.stamp = stamp++;
             P.level = 0;
-            if (n_seeds > 0) {
-                k_seed_select<<<std::max(1, std::min((n_seeds + 255) / 256, G.num_sms * 8)), 256, 0, st>>>(
-                    P, seeds, n_seeds, d_bad);
-                CND_CUDA_TRY(cudaGetLastError());
-                CND_CUDA_TRY(launch((const void *)k_finalize<0>, blocks_for((n_seeds + kNPW - 1) / kNPW, seed_blocks), st, P));
-            }
+            P.force = 1;
+            k_seed<<<1, 128, 0, st>>>(P, d_seg, 1, seeds, d_bad);
+            CND_CUDA_TRY(cudaGetLastError());
+            CND_CUDA_TRY(launch(k_fin_fn, fin_blocks, st, P));
+            P.force = 0;
             for (;;) {
                 CND_CUDA_TRY(cudaMemcpyAsync(hcnt, fr[cur].cnt, 4 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
                 CND_CUDA_TRY(cudaStreamSynchronize(st));
@@ -1245,15 +1454,16 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
                 P.out = fr[nx];
                 P.stamp = stamp++;
                 P.level += 1;
-                CND_CUDA_TRY(launch((const void *)k_push<0>, blocks_for(hcnt[2], push_blocks), st, P));
-                CND_CUDA_TRY(launch((const void *)k_finalize<1>, fin_blocks, st, P));
+                CND_CUDA_TRY(launch(k_push_fn, blocks_for(hcnt[2], push_blocks), st, P));
+                CND_CUDA_TRY(launch(k_fin_fn, fin_blocks, st, P));
                 cur = nx;
             }
             const int npb = 4096;
             dim3 grid((unsigned)((nw_here + 7) / 8), (unsigned)((n + npb - 1) / npb));
-            k_spread<<<grid, 256, 0, st>>>(P.vis, n, B, (int)nw_here, npb, spread_out + w0 * 64);
+            k_spread<<<grid, 256, 0, st>>>(P.vis, n, B, (int)nw_here, npb, d_wout, spread_out);
             CND_CUDA_TRY(cudaGetLastError());
-            k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, st>>>(P.vis, n, B, G.row_ptr, count_out, d_checks);
+            k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, st>>>(P.vis, n, B, G.row_ptr, nullptr, count_out,
+                                                                    d_checks);
             CND_CUDA_TRY(cudaGetLastError());
         }
     }

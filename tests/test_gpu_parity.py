@@ -241,3 +241,50 @@ def test_deferred_expansion_refuses_levels(er0):
     assert ei.value.status == P.CND_EINVAL
     with pytest.raises(P.CndError):
         sim("ic", G, seeds, 64, 1, defer_bits=4, level_counts_len=0, max_levels=3)
+
+
+def _batch_ref(model, g, p, w, seed_off, seeds, trials, keys, first_trial=0, want_counts=False):
+    spreads, counts, checks = [], [], 0
+    for i in range(len(trials)):
+        S = seeds[seed_off[i]:seed_off[i + 1]]
+        r = ref(model, g, S, int(trials[i]), int(keys[i]), p=p, w=w, first_trial=first_trial, level_counts_len=0)
+        spreads.append(r.spread)
+        counts.append(r.node_count)
+        checks += r.edge_checks
+    return np.concatenate(spreads) if spreads else np.zeros(0, np.int32), np.stack(counts), checks
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_batch_matches_items_one_by_one(rmat14, model):
+    """Items of uneven seed-set size and trial count, packed into shared passes."""
+    g, G, p, w, _ = rmat14
+    seed_off, seeds, trials, keys = I.batch_items(g.n, 23, 1, 40, (64, 100, 256, 7, 1000), graph_seed=4)
+    trials[3] = 0  # an empty item
+    f = P.cnd_ic_simulate_batch if model == "ic" else P.cnd_lt_simulate_batch
+    want_sp, want_nc, want_ck = _batch_ref(model, g, p, w, seed_off, seeds, trials, keys)
+    for wb in (0, 128, 640):
+        a = f(G, seed_off, seeds, trials, keys, node_count=True, edge_checks=True, word_bits=wb)
+        assert np.array_equal(a.spread, want_sp)
+        assert np.array_equal(a.node_count, want_nc)
+        assert a.edge_checks == want_ck
+
+
+def test_batch_device_pointers_and_offsets(ba):
+    torch = pytest.importorskip("torch")
+    g, G, p, w, _ = ba
+    seed_off, seeds, trials, keys = I.batch_items(g.n, 9, 1, 100, (256, 1024, 64), graph_seed=6)
+    want_sp, _, want_ck = _batch_ref("ic", g, p, w, seed_off, seeds, trials, keys, first_trial=128)
+    a = P.cnd_ic_simulate_batch(G, seed_off, torch.as_tensor(seeds, device="cuda"), trials, keys,
+                                edge_checks=True, first_trial=128)
+    torch.cuda.synchronize()
+    assert np.array_equal(a.spread.cpu().numpy(), want_sp)
+    assert a.edge_checks == want_ck
+
+
+def test_batch_single_item_equals_plain_call(er0):
+    g, G, p, w, seeds = er0
+    a = P.cnd_lt_simulate_batch(G, [0, len(seeds)], seeds, [1000], [4], node_count=True, edge_checks=True,
+                                level_counts_len=LC)
+    b = sim("lt", G, seeds, 1000, 4)
+    assert np.array_equal(a.spread, b.spread) and np.array_equal(a.node_count[0], b.node_count)
+    assert a.edge_checks == b.edge_checks and np.array_equal(a.level_counts, b.level_counts)
