@@ -1,26 +1,36 @@
 #!/usr/bin/env python
-"""Throughput of Monte Carlo IC + LT simulation on GB300 (one JSON line).
+"""Throughput of Monte Carlo IC / LT simulation on GB300 (one JSON line).
 
-A step is one pass of the whole path over one batch: an IC simulation and an
-LT simulation of the same workload (graph ingest happens once, before the
-timed region).  Default workload: Barabasi-Albert n=100,000 with 5
-attachments, undirected edges stored both ways (999,950 directed edges);
-weighted-cascade IC probabilities (fp32) and LT weights (uint32 fixed point);
-the 50 highest-degree nodes as seeds; 10,000 trials of each model.
+A step is one pass of the whole path over one batch of synthetic input (graph
+ingest happens once, before the timed region):
 
-value  = edge checks per second over the whole job (IC + LT, all ranks),
-         device-resident inputs, CUDA-event time of each step, L2 flushed
-         between steps.
-e2e    = the same metric through the host-pointer C-ABI calls (seeds copied
-         in, spreads / counts / edge checks copied out inside the timed region).
-roofline = the dominant expansion kernel: algorithmic bytes it must move
-         (counted by the kernels themselves) / its CUDA-event time.
-cpu_baseline = the CPU oracle on a bounded sample of the same workload, on
-         all host cores.
+  ba100k (default)  Barabasi-Albert n=100,000, 5 attachments, undirected edges
+                    stored both ways (999,950 directed edges); weighted-cascade
+                    IC probabilities (fp32) and LT weights (uint32 fixed point);
+                    the 50 highest-degree nodes as seeds; one IC and one LT
+                    simulation of 10,000 trials each.
+  rmat24            R-MAT scale 24, edge factor 16 (2^28 samples, deduplicated:
+                    263,430,501 edges); IC with p = 0.01 and LT with weighted-
+                    cascade weights; 100 highest-degree seeds; a sample of the
+                    100,000 trials per model (--trials, default 16384).
+  rmat20batch       R-MAT scale 20, 2^24 samples (16,084,954 edges), p ~ U[0,0.1)
+                    per edge; one batched IC call over the first K of 4,096 seed
+                    sets (|S| ~ U{1..100}, trials from {256, 1024, 4096}).
+  er1k              directed ER n=1,000, m=10,000, p=0.1, 10 seeds, 1,000 trials.
 
---impl reference times the CPU oracle alone (each step a bounded sample).
-Multi-GPU (torchrun): every rank simulates its own trial range of the same
-workload (weak scaling, no collective on the data path).
+value        = edge checks per second over the whole job (all ranks), device-
+               resident inputs, CUDA-event time of each step, L2 flushed
+               between steps outside the step events.
+e2e          = the same metric through the host-pointer C-ABI calls (seeds copied
+               in, spreads / counts / edge checks copied out).
+roofline     = the dominant expansion kernel: algorithmic bytes it must move
+               (counted by the kernels) / its CUDA-event time.
+cpu_baseline = the CPU oracle on a bounded sample of the same workload, on all
+               host cores.
+--impl reference times the CPU oracle alone, each step a bounded sample.
+Multi-GPU (torchrun): every rank simulates its own trials (single workloads:
+its own trial range; batches: its own seed sets) -- weak scaling, no collective
+on the data path.
 """
 from __future__ import annotations
 
@@ -47,22 +57,92 @@ FALLBACK_HBM_GBS = 6800.0
 
 
 # ----------------------------------------------------------------------------- workloads
-def make_workload(name: str):
+class Workload:
+    """A graph, its per-model edge data, seeds and the calls of one step."""
+
+    def __init__(self, name, desc, g, models, seeds=None, trials=0, rng_seed=1, batch=None, cpu=None):
+        self.name, self.desc, self.g = name, desc, g
+        self.models = models          # {"ic": p or None, "lt": w or None}
+        self.seeds, self.trials, self.rng_seed = seeds, trials, rng_seed
+        self.batch = batch            # (seed_off, seeds, trials, keys) or None
+        self.cpu = cpu or {}          # CPU-oracle sample sizes
+
+    def create(self, P):
+        return P.cnd_graph_create(self.g.n, self.g.row_ptr, self.g.col, self.models.get("ic"),
+                                  self.models.get("lt"))
+
+    def rank_batch(self, rank):
+        seed_off, seeds, trials, keys = self.batch
+        k = len(trials)
+        return seed_off, seeds, trials, keys, k
+
+    def calls(self, P, G, seeds_arg, rank, stats=0):
+        """One step: a list of (model, SimResult)."""
+        out = []
+        if self.batch is None:
+            first = rank * (((self.trials + 63) // 64) * 64)
+            for model in ("ic", "lt"):
+                if self.models.get(model) is None:
+                    continue
+                f = P.cnd_ic_simulate_ex if model == "ic" else P.cnd_lt_simulate_ex
+                out.append((model, f(G, seeds_arg, self.trials, self.rng_seed, first_trial=first, edge_checks=True,
+                                     stats=stats)))
+        else:
+            seed_off, _, trials, keys = self.batch
+            out.append(("ic", P.cnd_ic_simulate_batch(G, seed_off, seeds_arg, trials, keys, edge_checks=True,
+                                                      stats=stats)))
+        return out
+
+    def host_seeds(self):
+        return self.seeds if self.batch is None else self.batch[1]
+
+    def trials_per_step(self):
+        if self.batch is None:
+            return self.trials * sum(1 for m in ("ic", "lt") if self.models.get(m) is not None)
+        return int(np.asarray(self.batch[2], dtype=np.int64).sum())
+
+    def io_bytes(self):
+        """Bytes copied in / out per step by the host-pointer calls."""
+        if self.batch is None:
+            k = sum(1 for m in ("ic", "lt") if self.models.get(m) is not None)
+            return k * self.seeds.size * 4, k * (self.trials * 4 + self.g.n * 4 + 8)
+        return self.batch[1].size * 4, self.trials_per_step() * 4 + 8
+
+
+def make_workload(name: str, trials: int = 0, items: int = 0) -> Workload:
     if name == "ba100k":
         g = I.barabasi_albert(100_000, 5, graph_seed=1)
-        return dict(
-            name=name, g=g, p=I.ic_weighted_cascade(g), w=I.lt_weighted_cascade(g),
-            seeds=I.top_degree_seeds(g, 50), trials=10_000, rng_seed=1,
-            desc=(f"BA n=100000 m_attach=5 symmetrised ({g.m} directed edges), weighted-cascade IC (fp32 p=1/indeg) "
-                  "and LT (uint32 floor((2^32-1)/indeg)), 50 top-degree seeds, 10000 trials per model, rng_seed=1"),
-            cpu_trials=(2048, 1536))
+        T = trials or 10_000
+        return Workload(
+            name, f"BA n=100000 m_attach=5 symmetrised ({g.m} directed edges), weighted-cascade IC (fp32 "
+                  f"p=1/indeg) and LT (uint32 floor((2^32-1)/indeg)), 50 top-degree seeds, {T} trials per model, "
+                  "rng_seed=1",
+            g, {"ic": I.ic_weighted_cascade(g), "lt": I.lt_weighted_cascade(g)}, seeds=I.top_degree_seeds(g, 50),
+            trials=T, cpu={"ic": 2048, "lt": 1536})
     if name == "er1k":
         g = I.erdos_renyi_m(1000, 10_000, graph_seed=1)
-        return dict(
-            name=name, g=g, p=I.ic_uniform(g, 0.1), w=I.lt_weighted_cascade(g),
-            seeds=I.uniform_seeds(g.n, 10, 1), trials=1000, rng_seed=1,
-            desc="directed ER n=1000 m=10000, IC p=0.1, LT weighted cascade, 10 uniform seeds, 1000 trials per model",
-            cpu_trials=(1000, 1000))
+        T = trials or 1000
+        return Workload(
+            name, f"directed ER n=1000 m=10000, IC p=0.1, LT weighted cascade, 10 uniform seeds, {T} trials per model",
+            g, {"ic": I.ic_uniform(g, 0.1), "lt": I.lt_weighted_cascade(g)}, seeds=I.uniform_seeds(g.n, 10, 1),
+            trials=T, cpu={"ic": 1000, "lt": 1000})
+    if name == "rmat24":
+        g = I.rmat(24, 16 << 24, graph_seed=1)
+        T = trials or 16384
+        return Workload(
+            name, f"R-MAT scale 24 edge factor 16 (a,b,c,d=.57,.19,.19,.05; {g.m} directed edges after dedup), IC "
+                  f"p=0.01 and LT weighted cascade, 100 top-degree seeds, {T} of the 100000 trials per model",
+            g, {"ic": I.ic_uniform(g, 0.01), "lt": I.lt_weighted_cascade(g)}, seeds=I.top_degree_seeds(g, 100),
+            trials=T, cpu={"ic": 16, "lt": 16})
+    if name == "rmat20batch":
+        g = I.rmat(20, 1 << 24, graph_seed=1)
+        so, seeds, tr, keys = I.batch_items(g.n, 4096, 1, 100, (256, 1024, 4096), graph_seed=1)
+        k = items or 64
+        batch = (so[:k + 1], seeds[:so[k]], tr[:k], keys[:k])
+        return Workload(
+            name, f"R-MAT scale 20 ({g.m} directed edges), IC p~U[0,0.1) fp32 per edge, batched: the first {k} of "
+                  "4096 seed sets (|S|~U{1..100}, trials from {256,1024,4096}, rng_seed i+1) in one call",
+            g, {"ic": I.ic_uniform_random(g, 0.1, graph_seed=1)}, batch=batch, cpu={"items": 2, "trials": 16})
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -86,8 +166,9 @@ def measured_peak():
 
 def source_hash() -> str:
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(os.path.join(ROOT, "paper_2404_17059_gb300", "csrc"))):
-        with open(os.path.join(ROOT, "paper_2404_17059_gb300", "csrc", fn), "rb") as f:
+    d = os.path.join(ROOT, "paper_2404_17059_gb300", "csrc")
+    for fn in sorted(os.listdir(d)):
+        with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -172,22 +253,44 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(wl, rank):
-    """The oracle, as it stands, on a bounded sample of the workload's trials over all host cores."""
+def oracle_sample(wl: Workload, first: int = 0):
+    """The oracle, as it stands, on a bounded sample of the workload over all host cores.
+
+    Returns (edge checks, trials, seconds, description)."""
     import oracle
     cores = len(os.sched_getaffinity(0))
-    n_ic, n_lt = wl["cpu_trials"]
+    checks = trials = 0
+    parts = []
     t0 = time.perf_counter()
-    a = oracle.simulate_threads("ic", wl["g"], wl["seeds"], n_ic, wl["rng_seed"], ic_prob=wl["p"], threads=cores,
-                                level_counts_len=0)
-    b = oracle.simulate_threads("lt", wl["g"], wl["seeds"], n_lt, wl["rng_seed"], lt_weight=wl["w"],
-                                threads=cores, level_counts_len=0)
+    if wl.batch is None:
+        for model in ("ic", "lt"):
+            data = wl.models.get(model)
+            if data is None:
+                continue
+            n = wl.cpu[model]
+            kw = {"ic_prob": data} if model == "ic" else {"lt_weight": data}
+            r = oracle.simulate_threads(model, wl.g, wl.seeds, n, wl.rng_seed, threads=cores, level_counts_len=0,
+                                        first_trial=first, **kw)
+            checks += r.edge_checks
+            trials += n
+            parts.append(f"{model.upper()} trials {first}..{first + n - 1}")
+    else:
+        seed_off, seeds, tr, keys = wl.batch
+        for i in range(wl.cpu["items"]):
+            n = min(int(tr[i]), wl.cpu["trials"])
+            r = oracle.simulate_threads("ic", wl.g, seeds[seed_off[i]:seed_off[i + 1]], n, int(keys[i]),
+                                        threads=cores, level_counts_len=0, first_trial=first, ic_prob=wl.models["ic"])
+            checks += r.edge_checks
+            trials += n
+        parts.append(f"{wl.cpu['trials']} trials of each of the first {wl.cpu['items']} seed sets")
     dt = time.perf_counter() - t0
-    checks = a.edge_checks + b.edge_checks
+    return checks, trials, dt, ", ".join(parts) + f" on {cores} threads", cores
+
+
+def cpu_baseline(wl: Workload):
+    checks, trials, dt, desc, cores = oracle_sample(wl)
     return {"value": checks / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"trials 0..{n_ic - 1} (IC) and 0..{n_lt - 1} (LT) of the same workload, {checks} edge checks "
-                      f"in {dt:.2f} s wall on {cores} threads",
-            "trials_per_s": (n_ic + n_lt) / dt}
+            "sample": f"{desc}: {checks} edge checks in {dt:.2f} s wall", "trials_per_s": trials / dt}
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -195,30 +298,26 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
-    wl = make_workload(args.workload)
-    cores = len(os.sched_getaffinity(0))
-    n_ic, n_lt = args.ref_trials
-    times, checks = [], 0
+    wl = make_workload(args.workload, args.trials, args.items)
+    if args.ref_trials:
+        for m, n in zip(("ic", "lt"), args.ref_trials):
+            if m in wl.cpu:
+                wl.cpu[m] = n
+    times, checks, cores, desc = [], 0, 1, ""
     for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        a = oracle.simulate_threads("ic", wl["g"], wl["seeds"], n_ic, wl["rng_seed"], ic_prob=wl["p"],
-                                    threads=cores, level_counts_len=0, first_trial=64 * i)
-        b = oracle.simulate_threads("lt", wl["g"], wl["seeds"], n_lt, wl["rng_seed"], lt_weight=wl["w"],
-                                    threads=cores, level_counts_len=0, first_trial=64 * i)
-        dt = time.perf_counter() - t0
+        c, _, dt, desc, cores = oracle_sample(wl, first=64 * i)
         if i >= args.warmup:
             times.append(dt)
-            checks += a.edge_checks + b.edge_checks
+            checks += c
     total = sum(times)
     value = checks / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "sample_per_step": f"{n_ic} IC + {n_lt} LT trials"},
+        "config": {"workload": wl.desc, "name": wl.name, "sample_per_step": desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{n_ic} IC + {n_lt} LT trials per step over {cores} threads"},
+                         "sample": f"each step: {desc}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -226,6 +325,15 @@ def run_reference(args):
 
 
 # ----------------------------------------------------------------------------- our arm
+KERNEL = {"ic": "k_push<0>", "lt": "k_push<1>"}
+
+
+def alg_bytes(model, s):
+    """Bytes the expansion kernel must move, from its own work counters (kernels)."""
+    base = 8 * s["work_items"] + 8 * s["frontier_words"] + 8 * s["edges_scanned"] + 8 * s["word_checks"]
+    return base + (16 if model == "ic" else 8) * s["updates"]
+
+
 def run_ours(args):
     import torch
     import paper_2404_17059_gb300 as P
@@ -241,91 +349,74 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    wl = make_workload(args.workload)
-    if args.trials:
-        wl["trials"] = args.trials
-    g, T = wl["g"], wl["trials"]
-    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, wl["p"], wl["w"])
+    wl = make_workload(args.workload, args.trials, args.items)
+    if wl.batch is not None and world > 1:
+        # each rank its own seed sets: a disjoint slice of the 4096-item list
+        g = wl.g
+        so, seeds, tr, keys = I.batch_items(g.n, 4096, 1, 100, (256, 1024, 4096), graph_seed=1)
+        k = len(wl.batch[2])
+        a, b = rank * k, (rank + 1) * k
+        wl.batch = (so[a:b + 1] - so[a], seeds[so[a]:so[b]], tr[a:b], keys[a:b])
+    G = wl.create(P)
+    seeds_d = torch.as_tensor(wl.host_seeds(), device=dev)
     if args.profile_calls:
-        # one IC and one LT call with kernel-counted work (for ncu captures of those launches)
-        seeds_d = torch.as_tensor(wl["seeds"], device=dev)
-        out = {}
-        for model, f in (("ic", P.cnd_ic_simulate_ex), ("lt", P.cnd_lt_simulate_ex)):
-            r = f(G, seeds_d, T, wl["rng_seed"], edge_checks=True, stats=CND_STATS_COUNT)
-            out[model] = r.stats
+        out = {m: r.stats for m, r in wl.calls(P, G, seeds_d, rank, stats=CND_STATS_COUNT)}
         torch.cuda.synchronize()
-        print(json.dumps({"profile_calls": out, "workload": wl["name"], "trials": T, "src": source_hash()}))
+        print(json.dumps({"profile_calls": out, "workload": wl.name, "trials": wl.trials, "src": source_hash()}))
         return 0
-    seeds_d = torch.as_tensor(wl["seeds"], device=dev)
-    first = rank * (((T + 63) // 64) * 64)  # each rank its own trial range
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    def step(stats=0):
-        r_ic = P.cnd_ic_simulate_ex(G, seeds_d, T, wl["rng_seed"], first_trial=first, edge_checks=True,
-                                    stats=stats)
-        r_lt = P.cnd_lt_simulate_ex(G, seeds_d, T, wl["rng_seed"], first_trial=first, edge_checks=True,
-                                    stats=stats)
-        return r_ic, r_lt
-
-    # work counts for the roofline (untimed)
-    c_ic, c_lt = step(stats=CND_STATS_COUNT)
+    counted = dict(wl.calls(P, G, seeds_d, rank, stats=CND_STATS_COUNT))  # work counts (untimed)
     for _ in range(args.warmup):
-        step()
+        wl.calls(P, G, seeds_d, rank)
     torch.cuda.synchronize()
 
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    checks = 0
-    launches = 0
-    exp_ms = {"ic": 0.0, "lt": 0.0}
-    exp_n = {"ic": 0, "lt": 0}
-    fin_ms = {"ic": 0.0, "lt": 0.0}
+    checks = launches = 0
+    exp_ms, exp_n, fin_ms = {}, {}, {}
     wall0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
             flush.zero_()  # L2 flush (256 MiB write) outside the timed events
             ev[i][0].record(stream)
-            r_ic, r_lt = step(stats=CND_STATS_TIMING)
+            res = wl.calls(P, G, seeds_d, rank, stats=CND_STATS_TIMING)
             ev[i][1].record(stream)
-            checks += r_ic.edge_checks + r_lt.edge_checks
-            for k, r in (("ic", r_ic), ("lt", r_lt)):
+            for model, r in res:
+                checks += r.edge_checks
                 launches += r.stats["launches"]
-                exp_ms[k] += r.stats["expand_ms"]
-                exp_n[k] += r.stats["expand_launches"]
-                fin_ms[k] += r.stats["finalize_ms"]
+                exp_ms[model] = exp_ms.get(model, 0.0) + r.stats["expand_ms"]
+                exp_n[model] = exp_n.get(model, 0) + r.stats["expand_launches"]
+                fin_ms[model] = fin_ms.get(model, 0.0) + r.stats["finalize_ms"]
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
+    checks_all = float(checks)
     if dist:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-        c = torch.tensor([checks], dtype=torch.float64, device=dev)
+        c = torch.tensor([checks_all], dtype=torch.float64, device=dev)
         dist.all_reduce(c)
         checks_all = float(c.item())
-    else:
-        checks_all = float(checks)
     value = checks_all / (total_ms / 1e3)
-    trials_per_s = world * 2 * T * args.steps / (total_ms / 1e3)
+    trials_per_s = world * wl.trials_per_step() * args.steps / (total_ms / 1e3)
 
     # ---- end to end through the host-pointer API
-    seeds_h = wl["seeds"]
+    seeds_h = wl.host_seeds()
     torch.cuda.synchronize()
     e2e_checks = 0
     t0 = time.perf_counter()
     for i in range(args.steps):
-        a = P.cnd_ic_simulate_ex(G, seeds_h, T, wl["rng_seed"], first_trial=first, edge_checks=True)
-        b = P.cnd_lt_simulate_ex(G, seeds_h, T, wl["rng_seed"], first_trial=first, edge_checks=True)
-        e2e_checks += a.edge_checks + b.edge_checks
+        e2e_checks += sum(r.edge_checks for _, r in wl.calls(P, G, seeds_h, rank))
     e2e_s = time.perf_counter() - t0
-    h2d = 2 * seeds_h.size * 4
-    d2h = 2 * (T * 4 + g.n * 4 + 8)
+    h2d, d2h = wl.io_bytes()
 
     if dist:
         dist.destroy_process_group()
@@ -333,21 +424,19 @@ def run_ours(args):
         return 0
 
     # ---- roofline of the dominant expansion kernel (algorithmic bytes counted by the kernels)
-    def alg_bytes(model, s):
-        base = 8 * s["work_items"] + 8 * s["frontier_words"] + 8 * s["edges_scanned"] + 8 * s["word_checks"]
-        return base + (16 if model == "ic" else 8) * s["updates"]
-
     peak, peak_kind = measured_peak()
     kern = {}
-    for model, cs in (("ic", c_ic.stats), ("lt", c_lt.stats)):
+    for model, r in counted.items():
+        cs = r.stats
         n_l = max(1, cs["expand_launches"])
         bpl = alg_bytes(model, cs) / n_l
         avg_ms = exp_ms[model] / max(1, exp_n[model])
-        kern[model] = {"kernel": "k_push<0>" if model == "ic" else "k_push<1>", "launches_per_step": n_l,
-                       "avg_launch_ms": avg_ms, "alg_bytes_per_launch": bpl,
+        kern[model] = {"kernel": KERNEL[model], "launches_per_step": n_l, "avg_launch_ms": avg_ms,
+                       "alg_bytes_per_launch": bpl,
                        "achieved_gbs": bpl / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None,
                        "expand_ms_per_step": exp_ms[model] / args.steps,
                        "finalize_ms_per_step": fin_ms[model] / args.steps,
+                       "passes": cs["passes"], "word_bits": cs["word_bits"], "levels": cs["levels"],
                        "counts": {k: cs[k] for k in ("frontier_slots", "work_items", "edges_scanned",
                                                      "frontier_words", "word_checks", "draws", "updates")}}
     dom = max(kern, key=lambda k: kern[k]["expand_ms_per_step"])
@@ -355,18 +444,17 @@ def run_ours(args):
     ach = K["achieved_gbs"] or 0.0
     wc_per_launch = K["counts"]["word_checks"] / max(1, K["launches_per_step"])
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": ncu_traffic(K["kernel"], wl["name"], wc_per_launch), "kernel": K["kernel"],
+            "traffic": ncu_traffic(K["kernel"], wl.name, wc_per_launch), "kernel": K["kernel"],
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
 
-    cpu = None if args.no_cpu_baseline else cpu_baseline(wl, rank)
+    cpu = None if args.no_cpu_baseline else cpu_baseline(wl)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl["desc"], "name": wl["name"], "graph_nodes": g.n, "graph_edges": g.m,
-                   "trials_per_model_per_rank": T, "parallelism": f"trial-sharded x{world}",
-                   "l2": "flushed between timed steps (256 MiB write, outside the step events)",
-                   "word_bits": c_ic.stats["word_bits"]},
+        "config": {"workload": wl.desc, "name": wl.name, "graph_nodes": wl.g.n, "graph_edges": wl.g.m,
+                   "trials_per_step_per_rank": wl.trials_per_step(), "parallelism": f"trial-sharded x{world}",
+                   "l2": "flushed between timed steps (256 MiB write, outside the step events)"},
         "trials_per_s": trials_per_s,
         "edge_checks_per_step": checks_all / args.steps,
         "clocks": clk.summary(),
@@ -389,13 +477,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ba100k", choices=["ba100k", "er1k"])
+    ap.add_argument("--workload", default="ba100k", choices=["ba100k", "rmat24", "rmat20batch", "er1k"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trials", type=int, default=0, help="override the workload's trials per model")
+    ap.add_argument("--items", type=int, default=0, help="rmat20batch: seed sets per step (default 64)")
     ap.add_argument("--profile-calls", action="store_true",
-                    help="run one counted IC and one counted LT call only (for ncu captures)")
+                    help="run one counted step only (for ncu captures of its launches)")
     ap.add_argument("--ref-trials", type=int, nargs=2, default=(384, 256),
-                    help="IC and LT trials per reference step")
+                    help="IC and LT trials per reference step (single-seed-set workloads)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -41,11 +41,20 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _build_generator():
+    """Compile the synthetic-workload generator's C helper (gen/rmat_gen.c)."""
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    from paper_2404_17059_gb300 import inputs
+    inputs._genlib()
+
+
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(OUT, exist_ok=True)
     srcs = sources()
     headers = glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(ROOT, "include", "*.h"))
     if not force and not _stale(LIB, srcs + headers + [__file__]):
+        _build_generator()
         return LIB
     cc = nvcc()
 
@@ -61,6 +70,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
             print(r.stderr, file=sys.stderr)
         return obj
 
+    _build_generator()
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB + f".tmp{os.getpid()}"

@@ -85,16 +85,6 @@ def csr_from_edges(n: int, src: np.ndarray, dst: np.ndarray, name: str = "",
     return Graph(n=n, row_ptr=row_ptr.astype(np.int32), col=dst.astype(np.int32), name=name)
 
 
-def _dedup_keys(keys: np.ndarray) -> np.ndarray:
-    keys.sort()
-    if keys.size == 0:
-        return keys
-    keep = np.empty(keys.size, dtype=bool)
-    keep[0] = True
-    np.not_equal(keys[1:], keys[:-1], out=keep[1:])
-    return keys[keep]
-
-
 def erdos_renyi_m(n: int, m: int, graph_seed: int = 1) -> Graph:
     """Directed G(n, m): m distinct edges with uniform endpoints and no self-loops.
 
@@ -171,46 +161,70 @@ def barabasi_albert(n: int, m_attach: int, graph_seed: int = 1) -> Graph:
     return csr_from_edges(n, src, dst, name=f"ba_n{n}_m{m_attach}")
 
 
+_GEN_LIB = None
+
+
+def _genlib():
+    """ctypes handle of the C R-MAT generator (gen/rmat_gen.c), built with gcc on first use."""
+    global _GEN_LIB
+    if _GEN_LIB is None:
+        import ctypes as C
+        import os
+        import subprocess
+        here = os.path.dirname(os.path.abspath(__file__))
+        src = os.path.join(here, "gen", "rmat_gen.c")
+        out = os.path.join(here, "_build", "librmatgen.so")
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        if not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+            tmp = out + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-O3", "-std=c99", "-fPIC", "-shared", "-pthread", "-o", tmp, src])
+            os.replace(tmp, out)
+        L = C.CDLL(out)
+        L.rmat_keys.argtypes = [C.c_int, C.c_int64, C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.c_void_p]
+        L.rmat_keys.restype = None
+        L.sort_unique_u64.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_int, C.c_int]
+        L.sort_unique_u64.restype = C.c_int64
+        _GEN_LIB = L
+    return _GEN_LIB
+
+
 def rmat(scale: int, n_samples: int, a: float = 0.57, b: float = 0.19, c: float = 0.19,
-         graph_seed: int = 1, chunk: int = 1 << 23) -> Graph:
+         graph_seed: int = 1, threads: int | None = None) -> Graph:
     """R-MAT graph on n = 2^scale nodes from ``n_samples`` edge samples.
 
     Each sample descends ``scale`` levels of the adjacency matrix, choosing the
     quadrant (a: top-left, b: top-right, c: bottom-left, d: bottom-right) with
-    the given probabilities.  Probabilities are taken in units of 1/100, so the
-    usual (.57, .19, .19, .05) split is drawn exactly.  Self-loops and
-    duplicate edges are dropped, so m <= n_samples.
+    the given probabilities, taken in units of 1/100.  Draws come from a
+    counter-based stream per sample (gen/rmat_gen.c), so the graph depends only
+    on (scale, n_samples, probabilities, graph_seed).  Self-loops and duplicate
+    edges are dropped, so m <= n_samples; rows are sorted by target.
     """
+    import os
+    if scale < 1 or scale > 30:
+        raise ValueError("scale must be in 1..30")
     n = 1 << scale
     pa, pb, pc = int(round(a * 100)), int(round(b * 100)), int(round(c * 100))
     if min(pa, pb, pc) < 0 or pa + pb + pc > 100:
         raise ValueError("bad quadrant probabilities")
-    rng = _rng(graph_seed)
-    parts = []
-    done = 0
-    while done < n_samples:
-        k = min(chunk, n_samples - done)
-        s = np.zeros(k, dtype=np.int64)
-        d = np.zeros(k, dtype=np.int64)
-        for lvl in range(scale):
-            r = rng.integers(0, 100, size=k, dtype=np.uint8)
-            sbit = (r >= pa + pb).astype(np.int64)                       # c or d
-            dbit = (((r >= pa) & (r < pa + pb)) | (r >= pa + pb + pc)).astype(np.int64)  # b or d
-            shift = scale - 1 - lvl
-            s |= sbit << shift
-            d |= dbit << shift
-        keep = s != d
-        parts.append((s[keep] << 32) | d[keep])
-        done += k
-    keys = _dedup_keys(np.concatenate(parts))
-    src = (keys >> 32).astype(np.int64)
-    dst = (keys & 0xFFFFFFFF).astype(np.int64)
-    # keys are sorted by (src, dst): CSR order already
+    threads = threads or len(os.sched_getaffinity(0))
+    L = _genlib()
+    keys = np.empty(n_samples, dtype=np.uint64)
+    tmp = np.empty(n_samples, dtype=np.uint64)
+    L.rmat_keys(scale, n_samples, pa, pb, pc, int(graph_seed), threads, keys.ctypes.data)
+    m = L.sort_unique_u64(keys.ctypes.data, tmp.ctypes.data, n_samples, 64, threads)
+    del tmp
+    if m < 0:
+        raise MemoryError("R-MAT sort")
+    keys = keys[:m]
+    src = (keys >> np.uint64(32)).astype(np.int64)
     counts = np.bincount(src, minlength=n)
+    del src
     row_ptr = np.zeros(n + 1, dtype=np.int64)
     np.cumsum(counts, out=row_ptr[1:])
-    return Graph(n=n, row_ptr=row_ptr.astype(np.int32), col=dst.astype(np.int32),
-                 name=f"rmat_s{scale}_{n_samples}")
+    if row_ptr[-1] > np.iinfo(np.int32).max:
+        raise ValueError("edge count exceeds int32")
+    col = (keys & np.uint64(0xFFFFFFFF)).astype(np.int32)
+    return Graph(n=n, row_ptr=row_ptr.astype(np.int32), col=col, name=f"rmat_s{scale}_{n_samples}")
 
 
 def random_regular(n: int, d: int, graph_seed: int = 1, max_tries: int = 1000) -> Graph:
