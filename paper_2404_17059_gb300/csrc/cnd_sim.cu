@@ -138,25 +138,6 @@ __device__ __forceinline__ uint64_t word_g0(const Params &p, int w) {
     return PERWORD ? p.wg0[w] : p.g_base + 16ull * (uint64_t)w;
 }
 
-// IC: bits of `c` (trials of word w) whose edge e is live.  Coins come in
-// blocks of four trials, one Philox call per block that has a bit in c.
-template <bool PERWORD>
-__device__ __forceinline__ uint64_t ic_live_bits(const Params &p, int w, uint32_t e, uint64_t c, uint32_t thr,
-                                                 uint32_t &draws) {
-    const uint64_t g0 = word_g0<PERWORD>(p, w);
-    uint64_t live = 0;
-    while (c) {
-        ++draws;
-        const int j = (__ffsll((long long)c) - 1) >> 2;
-        const U4 r = draw<PERWORD>(p, w, e, g0 + (uint64_t)j, 0u);
-        const uint32_t nib = (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) | ((uint32_t)(r.z < thr) << 2) |
-                             ((uint32_t)(r.w < thr) << 3);
-        live |= (uint64_t)nib << (4 * j);
-        c &= ~(0xFull << (4 * j));
-    }
-    return live;
-}
-
 // Per-warp staging of the nodes a push lists for the finalize kernel: one
 // global atomic per 32 or more nodes instead of one per warp iteration.
 struct ListBuf {
@@ -440,11 +421,32 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
 // ---------------------------------------------------------------- push
 // One warp per work item: the item's (edge, pair) tasks are spread over the
 // lanes, task t = (edge t / k, pair t % k).
+// Nibble j of x non-zero -> bit j of the result (16 bits).
+__device__ __forceinline__ uint32_t nibble_mask(uint64_t x) {
+    uint64_t m = (x | (x >> 1) | (x >> 2) | (x >> 3)) & 0x1111111111111111ull;
+    m = (m | (m >> 3)) & 0x0303030303030303ull;
+    m = (m | (m >> 6)) & 0x000F000F000F000Full;
+    m = (m | (m >> 12)) & 0x000000FF000000FFull;
+    m = (m | (m >> 24)) & 0xFFFFull;
+    return (uint32_t)m;
+}
+
+// Per-warp queue that spreads the Philox calls of 32 IC tasks evenly over the
+// lanes: a task with many 4-trial blocks to draw no longer stalls the warp.
+struct DrawQueue {
+    uint16_t q[32 * 16];  // (lane << 4) | block
+    uint8_t res[32 * 16]; // live bits of the block's four trials
+    uint64_t g0[32];
+    uint32_t e[32], thr[32];
+    uint16_t w[32];
+};
+
 template <int MODEL, bool PERWORD>
 __global__ void __launch_bounds__(kBlock) k_push(Params p) {
     __shared__ uint64_t s_b[kWarps][kMaxB];
     __shared__ uint16_t s_w[kWarps][kMaxB];
     __shared__ int32_t s_list[kWarps][64];
+    __shared__ DrawQueue s_dq[MODEL == 0 ? kWarps : 1];
     const int lane = lane_id();
     const int wid = threadIdx.x >> 5;
     ListBuf lb{s_list[wid], 0};
@@ -478,6 +480,10 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
             const uint32_t t = t0 + lane;
             bool hit = false;
             int v = 0;
+            uint64_t ic_c = 0;
+            uint32_t ic_thr = 0;
+            int ic_e = 0, ic_w = 0, ic_v = 0;
+            size_t ic_idx = 0;
             if (t < T) {
                 const uint32_t el = div_by(t, (uint32_t)k, magic);
                 const int j = (int)(t - el * (uint32_t)k);
@@ -488,24 +494,15 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
                 const uint64_t f = s_b[wid][j];
                 const size_t idx = (size_t)v * B + w;
                 if (MODEL == 0) {
-                    const uint32_t thr = ed.y;
-                    if (thr != 0u) {
+                    ic_c = 0;
+                    ic_thr = ed.y;
+                    ic_e = e;
+                    ic_w = w;
+                    ic_v = v;
+                    ic_idx = idx;
+                    if (ic_thr != 0u) {
                         ++n_wc;
-                        const uint64_t c = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
-                        if (c) {
-                            uint64_t nb = c;
-                            if (thr != kAlways) nb &= ic_live_bits<PERWORD>(p, w, (uint32_t)e, c, thr, n_dr);
-                            if (nb) {
-                                nb &= ~(uint64_t)atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)nb);
-                                if (nb) {
-                                    const uint64_t old =
-                                        atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)nb);
-                                    mark_dirty(p, v, w, old);
-                                    ++n_up;
-                                    hit = true;
-                                }
-                            }
-                        }
+                        ic_c = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
                     }
                 } else {
                     const uint32_t wt = ed.y;
@@ -558,6 +555,74 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
                         }
                     }
                 }
+            }
+            if (MODEL == 0) {
+                // coins: the 4-trial blocks of c that need a draw, queued and drawn
+                // by all lanes; then the live bits go to vis / nxt
+                DrawQueue &dq = s_dq[MODEL == 0 ? wid : 0];
+                const uint64_t need = (ic_thr != kAlways) ? ic_c : 0ull;
+                const uint32_t nm = nibble_mask(need);
+                const int d = __popc(nm);
+                int base = d;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int x = __shfl_up_sync(kFull, base, o);
+                    if (lane >= o) base += x;
+                }
+                const int D = __shfl_sync(kFull, base, 31);
+                base -= d;
+                if (D > 0) {
+                    dq.g0[lane] = word_g0<PERWORD>(p, ic_w);
+                    dq.e[lane] = (uint32_t)ic_e;
+                    dq.thr[lane] = ic_thr;
+                    dq.w[lane] = (uint16_t)ic_w;
+                    {
+                        uint32_t mm = nm;
+                        int r = base;
+                        while (mm) {
+                            const int j = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            dq.q[r++] = (uint16_t)((lane << 4) | j);
+                        }
+                    }
+                    __syncwarp();
+                    for (int qi = lane; qi < D; qi += 32) {
+                        const uint32_t ent = dq.q[qi];
+                        const int o = (int)(ent >> 4), j = (int)(ent & 15u);
+                        const uint32_t th = dq.thr[o];
+                        const U4 r = draw<PERWORD>(p, dq.w[o], dq.e[o], dq.g0[o] + (uint64_t)j, 0u);
+                        dq.res[qi] = (uint8_t)((uint32_t)(r.x < th) | ((uint32_t)(r.y < th) << 1) |
+                                               ((uint32_t)(r.z < th) << 2) | ((uint32_t)(r.w < th) << 3));
+                        ++n_dr;
+                    }
+                    __syncwarp();
+                }
+                uint64_t nb = 0;
+                if (ic_c) {
+                    if (ic_thr == kAlways) {
+                        nb = ic_c;
+                    } else {
+                        uint64_t live = 0;
+                        uint32_t mm = nm;
+                        int r = base;
+                        while (mm) {
+                            const int j = __ffs(mm) - 1;
+                            mm &= mm - 1;
+                            live |= (uint64_t)dq.res[r++] << (4 * j);
+                        }
+                        nb = ic_c & live;
+                    }
+                }
+                if (nb) {
+                    nb &= ~(uint64_t)atomicOr((unsigned long long *)p.vis + ic_idx, (unsigned long long)nb);
+                    if (nb) {
+                        const uint64_t old = atomicOr((unsigned long long *)p.nxt + ic_idx, (unsigned long long)nb);
+                        mark_dirty(p, ic_v, ic_w, old);
+                        ++n_up;
+                        hit = true;
+                    }
+                }
+                __syncwarp();
             }
             lb.add(p, hit, v);
         }
