@@ -75,7 +75,7 @@ typedef int32_t cnd_status;
 #define CND_ETIMEOUT (-5)  /* host watchdog expired; outputs are not valid */
 #define CND_EOVERFLOW (-6) /* LT in-weights of a node sum above 2^32 - 1 */
 
-#define CND_DIR_AUTO 0 /* push or pull per step, by frontier size */
+#define CND_DIR_AUTO 0 /* push or pull per step, by frontier size (see pull_permille) */
 #define CND_DIR_PUSH 1
 #define CND_DIR_PULL 2
 
@@ -101,6 +101,7 @@ typedef struct cnd_sim_stats {
     int64_t word_checks;       /* (edge, word) pairs with frontier bits: target word read */
     int64_t draws;             /* Philox blocks drawn (IC coins; LT thresholds) */
     int64_t updates;           /* IC: target words that gained bits; LT: accumulator adds */
+    int64_t pull_steps;        /* expansion steps run in the pull direction */
 } cnd_sim_stats;
 
 /* Options of the *_ex entry points.  Zero-initialise (cnd_sim_opts_init). */
@@ -119,8 +120,9 @@ typedef struct cnd_sim_opts {
     int64_t *level_counts_out; /* NULL or level_counts_len values: [L] = number of
                                   (trial, node) pairs activated at step L */
     int32_t level_counts_len;
-    int32_t pull_permille;     /* AUTO: pull when the frontier's out-edges exceed this many
-                                  thousandths of m; 0 = built-in default */
+    int32_t pull_permille;     /* IC, AUTO: pull when the frontier's out-edges exceed this many
+                                  thousandths of m; 0 = push only (the measured default).  LT
+                                  always pushes */
     int32_t chunk_edges;       /* edges per push work item (0 = automatic) */
     int32_t defer_bits;        /* > 0: a node's word with fewer newly active trials than this may
                                   wait for more before its out-edges are examined; the spreads,

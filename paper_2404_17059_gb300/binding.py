@@ -56,6 +56,7 @@ class cnd_sim_stats(C.Structure):
         ("word_checks", C.c_int64),
         ("draws", C.c_int64),
         ("updates", C.c_int64),
+        ("pull_steps", C.c_int64),
     ]
 
     def as_dict(self):

@@ -46,6 +46,9 @@ namespace cnd {
 
 constexpr int kMaxB = 256;   // words per node per pass
 constexpr int kTasks = 256;  // (edge, pair) tasks per push work item
+// AUTO without pull_permille: push only -- the pull step measured 1.3x to 3.7x
+// slower than push on every GB300 workload here (hub in-rows scanned by one warp)
+constexpr int kPullPermille = 1001;
 constexpr int kWarps = 8;    // warps per block
 constexpr int kBlock = 32 * kWarps;
 
@@ -56,7 +59,7 @@ struct Frontier {
     uint16_t *pw = nullptr;    // [n*B] pool: word index
     uint64_t *pb = nullptr;    // [n*B] pool: frontier bits
     int2 *work = nullptr;      // [work_cap] (slot, first edge of the item within the row)
-    int32_t *cnt = nullptr;    // device [4]: pool pairs, slots (one 64-bit word), work items, listed nodes
+    int32_t *cnt = nullptr;    // device [4]: pool pairs, slots (one 64-bit word), work items, out-edges of the slots
 };
 
 struct Params {
@@ -78,6 +81,11 @@ struct Params {
     int32_t force;             // 1: expand every pending word
     RoundKeys rk;              // Philox round keys of rng_seed (all words share one key)
     const uint2 *wkey;         // [B] per-word Philox key (batches: words of different items)
+    // pull direction (IC): the frontier of the step, node-indexed
+    const int32_t *in_row_ptr;
+    const uint4 *in_edge;      // {src, edge id, IC threshold, LT weight}
+    uint64_t *fdense;          // [n*B] frontier words by node (zero outside the frontier)
+    uint32_t *fbits;           // [ceil(n/32)] frontier nodes
     const uint64_t *wg0;       // [B] per-word trial-block index of bit 0
     uint64_t g_base;           // trial-block index (trial >> 2) of bit 0 of word 0
     unsigned long long *level_counts;
@@ -237,7 +245,7 @@ constexpr int kNPB = kWarps * kNPW;     // nodes per block iteration
 // point (LT) unchanged.
 template <int MODE, bool PERWORD>
 __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
-    __shared__ int s_kept[kNPB], s_nch[kNPB], s_def[kNPB];
+    __shared__ int s_kept[kNPB], s_nch[kNPB], s_def[kNPB], s_deg[kNPB];
     __shared__ int s_off[kNPB], s_slot[kNPB], s_wb[kNPB], s_dpos[kNPB];
     const int lane = lane_id();
     const int wid = threadIdx.x >> 5;
@@ -332,6 +340,7 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
                 s_kept[wid * kNPW + h] = kept;
                 s_nch[wid * kNPW + h] = deg > 0 ? (deg + ne - 1) / ne : 0;
                 s_def[wid * kNPW + h] = deferred;
+                s_deg[wid * kNPW + h] = deg;
             }
         }
         __syncthreads();
@@ -354,6 +363,11 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
             }
             unsigned long long ps0 = 0;
             int item0 = 0, d0 = 0;
+            // out-edges of the new frontier (direction choice of the next step)
+            int dg = lane < kNPB ? s_deg[lane] : 0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) dg += __shfl_xor_sync(kFull, dg, o);
+            if (lane == 0 && dg) atomicAdd(&p.out.cnt[3], dg);
             if (lane == 31) {
                 if (sk) ps0 = atomicAdd((unsigned long long *)p.out.cnt, ((unsigned long long)sh << 32) | (unsigned)sk);
                 if (sc) item0 = atomicAdd(&p.out.cnt[2], sc);
@@ -636,6 +650,125 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
     count_add(p, C_UPDATES, n_up);
 }
 
+// ---------------------------------------------------------------- pull (IC)
+// Scatter (SET) or clear (!SET) the step's frontier in node-indexed form: one
+// warp per slot, lanes over its (word, bits) pairs.
+template <bool SET>
+__global__ void __launch_bounds__(kBlock) k_frontier_dense(Params p) {
+    const int lane = lane_id();
+    const int slots = p.in.cnt[1];
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    for (int sl = warp; sl < slots; sl += n_warps) {
+        const int u = p.in.node[sl];
+        const int off = p.in.poff[sl], k = p.in.pk[sl];
+        for (int j = lane; j < k; j += 32) p.fdense[(size_t)u * p.B + p.in.pw[off + j]] = SET ? p.in.pb[off + j] : 0ull;
+        if (lane == 0) {
+            if (SET) atomicOr(&p.fbits[u >> 5], 1u << (u & 31));
+            else atomicAnd(&p.fbits[u >> 5], ~(1u << (u & 31)));
+        }
+    }
+}
+
+// Pull step of IC: one warp per node v with trials where it is still inactive;
+// lanes own words.  The warp walks v's in-edges; for an in-neighbour u in the
+// frontier it draws the coins of edge (u, v) only for the trials where u is
+// newly active and v is still inactive -- trials activated by an earlier
+// in-edge in this step need no further coin -- and stops once every trial of
+// v is active.  v's words are written by this warp alone (no atomics).
+template <bool PERWORD>
+__global__ void __launch_bounds__(kBlock) k_pull_ic(Params p) {
+    constexpr int NW = kMaxB / 32;
+    __shared__ int32_t s_list[kWarps][64];
+    const int lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    ListBuf lb{s_list[wid], 0};
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int B = p.B;
+    uint32_t n_edges = 0, n_wc = 0, n_dr = 0, n_up = 0;
+    for (int v = warp; v < p.n; v += n_warps) {
+        uint64_t U[NW], nb[NW];
+        bool open = false;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int w = lane + 32 * k;
+            U[k] = w < B ? p.valid[w] & ~(uint64_t)p.vis[(size_t)v * B + w] : 0ull;
+            nb[k] = 0ull;
+            open |= U[k] != 0ull;
+        }
+        if (!__any_sync(kFull, open)) continue;
+        const int e0 = p.in_row_ptr[v], e1 = p.in_row_ptr[v + 1];
+        bool done = false;
+        for (int eb = e0; eb < e1 && !done; eb += 32) {
+            uint4 ie = make_uint4(0u, 0u, 0u, 0u);
+            if (eb + lane < e1) ie = __ldg(&p.in_edge[eb + lane]);
+            const bool fr = eb + lane < e1 && ie.z != 0u && ((p.fbits[ie.x >> 5] >> (ie.x & 31)) & 1u);
+            unsigned todo = __ballot_sync(kFull, fr);
+            if (lane == 0) n_edges += min(32, e1 - eb);
+            while (todo) {
+                const int sidx = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const uint32_t u = __shfl_sync(kFull, ie.x, sidx);
+                const uint32_t e = __shfl_sync(kFull, ie.y, sidx);
+                const uint32_t thr = __shfl_sync(kFull, ie.z, sidx);
+                bool still = false;
+#pragma unroll
+                for (int k = 0; k < NW; ++k) {
+                    if (U[k] == 0ull) continue;
+                    const int w = lane + 32 * k;
+                    const uint64_t f = p.fdense[(size_t)u * B + w] & U[k];
+                    ++n_wc;
+                    if (f) {
+                        uint64_t live = f;
+                        if (thr != kAlways) {
+                            live = 0;
+                            const uint64_t g0 = word_g0<PERWORD>(p, w);
+                            uint64_t c = f;
+                            while (c) {
+                                ++n_dr;
+                                const int j = (__ffsll((long long)c) - 1) >> 2;
+                                const U4 r = draw<PERWORD>(p, w, e, g0 + (uint64_t)j, 0u);
+                                const uint32_t nib = (uint32_t)(r.x < thr) | ((uint32_t)(r.y < thr) << 1) |
+                                                     ((uint32_t)(r.z < thr) << 2) | ((uint32_t)(r.w < thr) << 3);
+                                live |= (uint64_t)nib << (4 * j);
+                                c &= ~(0xFull << (4 * j));
+                            }
+                            live &= f;
+                        }
+                        nb[k] |= live;
+                        U[k] &= ~live;
+                    }
+                    still |= U[k] != 0ull;
+                }
+                if (!__any_sync(kFull, still)) {
+                    done = true;
+                    break;
+                }
+            }
+        }
+        bool hit = false;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            if (nb[k] == 0ull) continue;
+            const int w = lane + 32 * k;
+            const size_t idx = (size_t)v * B + w;
+            p.vis[idx] |= nb[k];
+            p.nxt[idx] = nb[k];
+            atomicOr((unsigned long long *)(p.dmask + (size_t)v * p.nq + (w >> 6)), 1ull << (w & 63));
+            ++n_up;
+            hit = true;
+        }
+        const bool any_hit = __any_sync(kFull, hit);
+        lb.add(p, lane == 0 && any_hit, v);
+    }
+    if (lb.n) lb.flush(p);
+    count_add(p, C_EDGES, n_edges);
+    count_add(p, C_WCHECKS, n_wc);
+    count_add(p, C_DRAWS, n_dr);
+    count_add(p, C_UPDATES, n_up);
+}
+
 // ---------------------------------------------------------------- outputs
 // Per-trial spread: warp k of a block owns word w and reduces 32 nodes at a
 // time with one ballot per trial bit; trial b of word w lands at
@@ -906,6 +1039,17 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
         CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
         CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
     }
+    // pull direction (IC only): node-indexed frontier and frontier-node bitmap
+    const bool may_pull = model == 0 && o.direction != CND_DIR_PUSH && G.m > 0;
+    const int permille = o.pull_permille > 0 ? o.pull_permille : kPullPermille;
+    if (may_pull) {
+        CND_CUDA_TRY(W.alloc(&P.fdense, nB));
+        CND_CUDA_TRY(W.alloc(&P.fbits, (size_t)(n + 31) / 32));
+        CND_CUDA_TRY(cudaMemsetAsync(P.fdense, 0, sizeof(uint64_t) * nB, st));
+        CND_CUDA_TRY(cudaMemsetAsync(P.fbits, 0, sizeof(uint32_t) * ((size_t)(n + 31) / 32), st));
+        P.in_row_ptr = G.in_row_ptr;
+        P.in_edge = G.in_edge;
+    }
     for (int i = 0; i < 2; ++i) {
         CND_CUDA_TRY(W.alloc(&fr[i].node, (size_t)n));
         CND_CUDA_TRY(W.alloc(&fr[i].poff, (size_t)n));
@@ -933,6 +1077,9 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     const void *k_fin_uk = model == 0 ? (const void *)k_finalize<1, false> : (const void *)k_finalize<2, false>;
     const void *k_seedfin = (const void *)k_finalize<1, false>;
     const int push_blocks = G.num_sms * resident_blocks(k_push_uk);
+    const void *k_pull_pw = (const void *)k_pull_ic<true>, *k_pull_uk = (const void *)k_pull_ic<false>;
+    const int pull_blocks = G.num_sms * resident_blocks(k_pull_uk);
+    const int dense_blocks = G.num_sms * resident_blocks((const void *)k_frontier_dense<true>);
     const int fin_blocks = G.num_sms * resident_blocks(k_fin_uk);
     const int seed_blocks = G.num_sms * resident_blocks(k_seedfin);
     uint32_t stamp = 0;
@@ -1006,7 +1153,7 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
                 if (ts != CND_OK) return ts;
             }
             // slots / work items of step L's frontier; nodes whose words wait
-            const int32_t slots = hcnt[1], n_items_w = hcnt[2], waiting = hcnt[4];
+            const int32_t slots = hcnt[1], n_items_w = hcnt[2], front_edges = hcnt[3], waiting = hcnt[4];
             if (S) {
                 S->frontier_slots += slots;
                 S->work_items += n_items_w;
@@ -1038,8 +1185,18 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
             P.level = L + 1;
             // nothing to expand in this step: every waiting word goes now
             P.force = n_items_w == 0 ? 1 : 0;
+            // direction: pull when the frontier's out-edges are a large share of m
+            const bool pull = may_pull && n_items_w > 0 && P.tau == 0 &&
+                              (o.direction == CND_DIR_PULL ||
+                               (int64_t)front_edges * 1000 > (int64_t)permille * (int64_t)G.m);
             if (timing) CND_CUDA_TRY(cudaEventRecord(ev.e[0], st));
-            if (n_items_w > 0) {
+            if (pull) {
+                CND_CUDA_TRY(launch((const void *)k_frontier_dense<true>, dense_blocks, st, P));
+                CND_CUDA_TRY(launch(pw ? k_pull_pw : k_pull_uk, pull_blocks, st, P));
+                CND_CUDA_TRY(launch((const void *)k_frontier_dense<false>, dense_blocks, st, P));
+                launches += 3;
+                if (S) S->pull_steps += 1;
+            } else if (n_items_w > 0) {
                 CND_CUDA_TRY(launch(k_push_fn, blocks_for(n_items_w, push_blocks), st, P));
                 launches += 1;
             }

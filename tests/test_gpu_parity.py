@@ -288,3 +288,35 @@ def test_batch_single_item_equals_plain_call(er0):
     b = sim("lt", G, seeds, 1000, 4)
     assert np.array_equal(a.spread, b.spread) and np.array_equal(a.node_count[0], b.node_count)
     assert a.edge_checks == b.edge_checks and np.array_equal(a.level_counts, b.level_counts)
+
+
+def test_pull_direction_same_results(er0, ba, rmat14):
+    """IC steps expanded by pulling over in-edges give the same trials, counts and steps."""
+    for fx in (er0, ba, rmat14):
+        g, G, p, w, seeds = fx
+        b = ref("ic", g, seeds, 320, 6, p=p)
+        for kw in ({"direction": "pull"}, {"direction": "auto", "pull_permille": 1},
+                   {"direction": "auto", "pull_permille": 200}, {"direction": "pull", "word_bits": 64}):
+            a = sim("ic", G, seeds, 320, 6, stats=2, **kw)
+            assert_same(a, b)
+            if kw.get("direction") == "pull":
+                assert a.stats["pull_steps"] > 0
+        # LT has no pull step: the option leaves it pushing
+        bl = ref("lt", g, seeds, 128, 6, w=w)
+        assert_same(sim("lt", G, seeds, 128, 6, direction="pull"), bl)
+
+
+def test_pull_direction_batch_and_edge_cases(rmat14):
+    g, G, p, w, _ = rmat14
+    seed_off, seeds, trials, keys = I.batch_items(g.n, 9, 1, 30, (64, 200, 500), graph_seed=8)
+    want_sp, want_nc, want_ck = _batch_ref("ic", g, p, w, seed_off, seeds, trials, keys)
+    a = P.cnd_ic_simulate_batch(G, seed_off, seeds, trials, keys, node_count=True, edge_checks=True,
+                                direction="pull")
+    assert np.array_equal(a.spread, want_sp) and np.array_equal(a.node_count, want_nc) and a.edge_checks == want_ck
+    src = np.array([0, 0, 0, 1, 2, 2, 3, 5, 5, 6, 7, 7])
+    dst = np.array([1, 1, 2, 3, 2, 4, 5, 6, 7, 8, 8, 0])
+    g2 = I.csr_from_edges(10, src, dst, sort=False)
+    p2 = np.array([0.5, 0.5, 1.0, 0.0, 0.7, 1.0, 0.9, 0.3, 0.6, 1.0, 0.2, 0.4], dtype=np.float32)
+    G2 = P.cnd_graph_create(g2.n, g2.row_ptr, g2.col, p2, None)
+    for seeds2 in ([0], [9], [0, 0, 3, 3], list(range(10))):
+        assert_same(sim("ic", G2, seeds2, 300, 5, direction="pull"), ref("ic", g2, seeds2, 300, 5, p=p2))
