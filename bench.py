@@ -76,7 +76,7 @@ class Workload:
         k = len(trials)
         return seed_off, seeds, trials, keys, k
 
-    def calls(self, P, G, seeds_arg, rank, stats=0):
+    def calls(self, P, G, seeds_arg, rank, stats=0, graph=0):
         """One step: a list of (model, SimResult)."""
         out = []
         if self.batch is None:
@@ -86,11 +86,11 @@ class Workload:
                     continue
                 f = P.cnd_ic_simulate_ex if model == "ic" else P.cnd_lt_simulate_ex
                 out.append((model, f(G, seeds_arg, self.trials, self.rng_seed, first_trial=first, edge_checks=True,
-                                     stats=stats)))
+                                     stats=stats, graph=graph)))
         else:
             seed_off, _, trials, keys = self.batch
             out.append(("ic", P.cnd_ic_simulate_batch(G, seed_off, seeds_arg, trials, keys, edge_checks=True,
-                                                      stats=stats)))
+                                                      stats=stats, graph=graph)))
         return out
 
     def host_seeds(self):
@@ -408,6 +408,16 @@ def run_ours(args):
     value = checks_all / (total_ms / 1e3)
     trials_per_s = world * wl.trials_per_step() * args.steps / (total_ms / 1e3)
 
+    # ---- the same steps as one CUDA-graph launch per call (device-side step loop; no per-kernel events)
+    ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        flush.zero_()
+        ev_g[i][0].record(stream)
+        wl.calls(P, G, seeds_d, rank, graph=1)
+        ev_g[i][1].record(stream)
+    torch.cuda.synchronize()
+    graph_ms = sum(a.elapsed_time(b) for a, b in ev_g) / args.steps
+
     # ---- end to end through the host-pointer API
     seeds_h = wl.host_seeds()
     torch.cuda.synchronize()
@@ -456,6 +466,8 @@ def run_ours(args):
                    "trials_per_step_per_rank": wl.trials_per_step(), "parallelism": f"trial-sharded x{world}",
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)"},
         "trials_per_s": trials_per_s,
+        "graph_mode": {"ms_per_step": graph_ms, "value": checks_all / args.steps / (graph_ms / 1e3),
+                       "note": "same steps, one CUDA-graph launch per call (opts.graph=1)"},
         "edge_checks_per_step": checks_all / args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": world * e2e_checks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,

@@ -134,7 +134,10 @@ typedef struct cnd_sim_opts {
     cnd_sim_stats *stats;      /* NULL or host struct filled by the call */
     int32_t defer_steps;       /* with defer_bits: a word waits at most this many steps (0 = until
                                   nothing else is left to expand) */
-    int32_t reserved1;
+    int32_t graph;             /* 1: run the whole call as one CUDA graph launch -- every pass
+                                  and its step loop (a device-side WHILE node whose condition a
+                                  one-thread control kernel sets after each step), no host round
+                                  trip per step; ignored with CND_STATS_TIMING */
     int64_t reserved[2];
 } cnd_sim_opts;
 

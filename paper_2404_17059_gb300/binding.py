@@ -80,7 +80,7 @@ class cnd_sim_opts(C.Structure):
         ("timeout_s", C.c_double),
         ("stats", C.c_void_p),
         ("defer_steps", C.c_int32),
-        ("reserved1", C.c_int32),
+        ("graph", C.c_int32),
         ("reserved", C.c_int64 * 2),
     ]
 
@@ -214,7 +214,7 @@ class SimResult:
 def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=True, node_count=True,
               first_trial=0, max_levels=0, direction="auto", word_bits=0, level_counts_len=0,
               edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None, stats=0,
-              defer_bits=0, defer_steps=0):
+              defer_bits=0, defer_steps=0, graph=0):
     L = load()
     n_trials = int(n_trials)
     dev = _is_torch_cuda(seeds)
@@ -260,6 +260,7 @@ def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=Tru
         o.chunk_edges = int(chunk_edges)
         o.defer_bits = int(defer_bits)
         o.defer_steps = int(defer_steps)
+        o.graph = int(graph)
         o.timeout_s = float(timeout_s)
         stt = None
         if stats:

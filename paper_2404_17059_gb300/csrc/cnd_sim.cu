@@ -62,6 +62,17 @@ struct Frontier {
     int32_t *cnt = nullptr;    // device [4]: pool pairs, slots (one 64-bit word), work items, out-edges of the slots
 };
 
+// Step state of a run whose step loop executes on the device (CUDA-graph mode).
+struct Ctl {
+    int32_t level;   // step being run: frontier fr[level & 1] -> fr[(level + 1) & 1]; -1: the seed step
+    uint32_t stamp;  // stamp of that step
+    int32_t force;   // 1: every waiting word is expanded now
+    int32_t pull;    // 1: this step pulls (IC)
+    int32_t limit;   // a pass stopped at max_levels with trials still active
+    int32_t pad;
+    unsigned long long slots, items, levels, pull_steps;
+};
+
 struct Params {
     int32_t n, B, nq;
     int32_t chunk;             // > 0: fixed edges per work item
@@ -94,7 +105,28 @@ struct Params {
     const uint64_t *valid;     // [B] valid-trial mask of each word
     int32_t nvalid;            // words of this pass that hold trials
     unsigned long long *ctr;   // null, or [C_N] work counters (CND_STATS_COUNT)
+    // graph mode: the step's frontiers, lists and stamp come from ctl (resolve())
+    Ctl *ctl;
+    Frontier fr[2];
+    int32_t *lists[2];
+    int32_t *lcnt;             // [2] list counters
 };
+
+// In graph mode, point the step fields of p at this step's buffers.
+__device__ __forceinline__ void resolve(Params &p) {
+    if (!p.ctl) return;
+    const int L = p.ctl->level;
+    const bool odd = (L & 1) != 0;
+    p.in = odd ? p.fr[1] : p.fr[0];
+    p.out = odd ? p.fr[0] : p.fr[1];
+    p.lin = odd ? p.lists[1] : p.lists[0];
+    p.lin_cnt = p.lcnt + (odd ? 1 : 0);
+    p.lnext = odd ? p.lists[0] : p.lists[1];
+    p.lnext_cnt = p.lcnt + (odd ? 0 : 1);
+    p.stamp = p.ctl->stamp;
+    p.force = p.ctl->force;
+    p.level = L + 1;
+}
 
 enum { C_EDGES, C_FWORDS, C_WCHECKS, C_DRAWS, C_UPDATES, C_N };
 
@@ -189,8 +221,10 @@ struct SeedSeg {
 // Step 0: every seed is active in every valid trial of its item's words.  The
 // words go to nxt (dirty) and the seed to the list, so the seed step is then
 // finalized like an IC step.  Duplicate seeds write the same words.
-__global__ void k_seed(Params p, const SeedSeg *__restrict__ segs, int32_t n_segs, const int32_t *__restrict__ seeds,
+__global__ void k_seed(Params p_, const SeedSeg *__restrict__ segs, int32_t n_segs, const int32_t *__restrict__ seeds,
                        int32_t *__restrict__ bad) {
+    Params p = p_;
+    resolve(p);
     for (int j = blockIdx.x; j < n_segs; j += gridDim.x) {
         const SeedSeg sg = segs[j];
         for (int i = sg.s_begin + (int)threadIdx.x; i < sg.s_end; i += blockDim.x) {
@@ -244,7 +278,9 @@ constexpr int kNPB = kWarps * kNPW;     // nodes per block iteration
 // later, merged with later bits, leaves reachability (IC) and the least fixed
 // point (LT) unchanged.
 template <int MODE, bool PERWORD>
-__global__ void __launch_bounds__(kBlock) k_finalize(Params p) {
+__global__ void __launch_bounds__(kBlock) k_finalize(Params p_) {
+    Params p = p_;
+    resolve(p);
     __shared__ int s_kept[kNPB], s_nch[kNPB], s_def[kNPB], s_deg[kNPB];
     __shared__ int s_off[kNPB], s_slot[kNPB], s_wb[kNPB], s_dpos[kNPB];
     const int lane = lane_id();
@@ -456,7 +492,10 @@ struct DrawQueue {
 };
 
 template <int MODEL, bool PERWORD>
-__global__ void __launch_bounds__(kBlock) k_push(Params p) {
+__global__ void __launch_bounds__(kBlock) k_push(Params p_) {
+    Params p = p_;
+    resolve(p);
+    if (p.ctl && p.ctl->pull) return;  // graph mode: this step pulls
     __shared__ uint64_t s_b[kWarps][kMaxB];
     __shared__ uint16_t s_w[kWarps][kMaxB];
     __shared__ int32_t s_list[kWarps][64];
@@ -654,7 +693,10 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p) {
 // Scatter (SET) or clear (!SET) the step's frontier in node-indexed form: one
 // warp per slot, lanes over its (word, bits) pairs.
 template <bool SET>
-__global__ void __launch_bounds__(kBlock) k_frontier_dense(Params p) {
+__global__ void __launch_bounds__(kBlock) k_frontier_dense(Params p_) {
+    Params p = p_;
+    resolve(p);
+    if (p.ctl && !p.ctl->pull) return;
     const int lane = lane_id();
     const int slots = p.in.cnt[1];
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -677,7 +719,10 @@ __global__ void __launch_bounds__(kBlock) k_frontier_dense(Params p) {
 // in-edge in this step need no further coin -- and stops once every trial of
 // v is active.  v's words are written by this warp alone (no atomics).
 template <bool PERWORD>
-__global__ void __launch_bounds__(kBlock) k_pull_ic(Params p) {
+__global__ void __launch_bounds__(kBlock) k_pull_ic(Params p_) {
+    Params p = p_;
+    resolve(p);
+    if (p.ctl && !p.ctl->pull) return;
     constexpr int NW = kMaxB / 32;
     __shared__ int32_t s_list[kWarps][64];
     const int lane = lane_id();
@@ -767,6 +812,55 @@ __global__ void __launch_bounds__(kBlock) k_pull_ic(Params p) {
     count_add(p, C_WCHECKS, n_wc);
     count_add(p, C_DRAWS, n_dr);
     count_add(p, C_UPDATES, n_up);
+}
+
+// ---------------------------------------------------------------- device step loop
+// Start of a pass in graph mode: the seed step (-1) with a fresh stamp.
+__global__ void k_pass_begin(Params p) {
+    Ctl *c = p.ctl;
+    c->level = -1;
+    c->stamp += 1u;
+    c->force = 1;
+    c->pull = 0;
+}
+
+// The host loop's decision, on the device: run step L (the first step of a
+// pass, or the one after the step just finalized)?  Prepares its counters and
+// sets the WHILE condition of the pass's step loop.
+__global__ void k_ctl(Params p, cudaGraphConditionalHandle h, int32_t first, int32_t max_levels, int32_t may_pull,
+                      int32_t pull_always, int32_t permille, int64_t m, int32_t tau) {
+    Ctl *c = p.ctl;
+    const int L = first ? 0 : c->level + 1;
+    const bool odd = (L & 1) != 0;
+    const int32_t *cnt = odd ? p.fr[1].cnt : p.fr[0].cnt;
+    const int32_t slots = cnt[1], items = cnt[2], fedges = cnt[3];
+    const int32_t waiting = p.lcnt[odd ? 1 : 0];
+    c->slots += (unsigned long long)slots;
+    c->items += (unsigned long long)items;
+    int go = 1;
+    if (slots == 0 && waiting == 0) {
+        go = 0;
+    } else if (max_levels > 0 && L >= max_levels) {
+        c->limit = 1;
+        go = 0;
+    } else if (items == 0 && waiting == 0) {
+        go = 0;
+    }
+    if (go) {
+        int32_t *ncnt = odd ? p.fr[0].cnt : p.fr[1].cnt;
+        ncnt[0] = ncnt[1] = ncnt[2] = ncnt[3] = 0;
+        p.lcnt[odd ? 0 : 1] = 0;
+        c->level = L;
+        c->stamp += 1u;
+        c->force = items == 0 ? 1 : 0;
+        c->pull = (may_pull && items > 0 && tau == 0 &&
+                   (pull_always || (int64_t)fedges * 1000 > (int64_t)permille * m))
+                      ? 1
+                      : 0;
+        c->levels += 1ull;
+        c->pull_steps += (unsigned long long)c->pull;
+    }
+    cudaGraphSetConditional(h, (unsigned)go);
 }
 
 // ---------------------------------------------------------------- outputs
@@ -1012,25 +1106,70 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     CND_CUDA_TRY(W.alloc(&lists[0], (size_t)n));
     CND_CUDA_TRY(W.alloc(&lists[1], (size_t)n));
     CND_CUDA_TRY(W.alloc(&d_lcnt, 2));
-    // per-pass column descriptors, uploaded as one block:
+    // column descriptors of every pass, uploaded as one block; pass i's part:
     // valid[B] | wg0[B] | wout[B] | wkey[B] | witem[B] (+pad) | seed runs
     size_t max_runs = 0;
     for (const auto &ps : passes) max_runs = std::max(max_runs, ps.size());
     const size_t desc_words = 4 * (size_t)B + (size_t)(B + 1) / 2 + 2 * max_runs;
+    const size_t n_pass_all = passes.size();
     uint64_t *d_desc = nullptr;
-    CND_CUDA_TRY(W.alloc(&d_desc, desc_words));
-    std::vector<uint64_t> h_desc(desc_words, 0);
-    uint64_t *h_valid = h_desc.data(), *h_wg0 = h_valid + B;
-    int64_t *h_wout = (int64_t *)(h_wg0 + B);
-    uint2 *h_wkey = (uint2 *)(h_wout + B);
-    int32_t *h_witem = (int32_t *)(h_wkey + B);
-    SeedSeg *h_segs = (SeedSeg *)(h_desc.data() + 4 * (size_t)B + (size_t)(B + 1) / 2);
-    P.valid = d_desc;
-    P.wg0 = d_desc + B;
-    const int64_t *d_wout = (const int64_t *)(d_desc + 2 * (size_t)B);
-    P.wkey = (const uint2 *)(d_desc + 3 * (size_t)B);
-    const int32_t *d_witem = (const int32_t *)(d_desc + 4 * (size_t)B);
-    const SeedSeg *d_segs = (const SeedSeg *)(d_desc + 4 * (size_t)B + (size_t)(B + 1) / 2);
+    CND_CUDA_TRY(W.alloc(&d_desc, desc_words * n_pass_all));
+    std::vector<uint64_t> h_desc(desc_words * n_pass_all, 0);
+    struct PassInfo {
+        int32_t nw_here;
+        bool perword;
+        uint64_t key, g_base;
+    };
+    std::vector<PassInfo> pinfo(n_pass_all);
+    for (size_t pass = 0; pass < n_pass_all; ++pass) {
+        const std::vector<Seg> &ps = passes[pass];
+        uint64_t *hv = h_desc.data() + pass * desc_words, *hg = hv + B;
+        int64_t *ho = (int64_t *)(hg + B);
+        uint2 *hk = (uint2 *)(ho + B);
+        int32_t *hi = (int32_t *)(hk + B);
+        SeedSeg *hs = (SeedSeg *)(hv + 4 * (size_t)B + (size_t)(B + 1) / 2);
+        bool one_key = true;
+        int32_t nw_here = 0;
+        for (size_t r = 0; r < ps.size(); ++r) {
+            const Seg &sg = ps[r];
+            const ItemDesc &it = items[sg.item];
+            one_key = one_key && it.key == items[ps[0].item].key;
+            for (int32_t c = 0; c < sg.cnt; ++c) {
+                const int32_t col = sg.col0 + c;
+                const int64_t lw = sg.lw0 + c;
+                const int64_t left = it.trials - 64 * lw;
+                hv[col] = left >= 64 ? ~0ull : ((1ull << left) - 1ull);
+                hg[col] = (uint64_t)(o.first_trial + 64 * lw) >> 2;
+                ho[col] = it.out0 + 64 * lw;
+                hk[col] = make_uint2((uint32_t)it.key, (uint32_t)(it.key >> 32));
+                hi[col] = sg.item;
+            }
+            hs[r] = SeedSeg{(int32_t)it.seed_begin, (int32_t)it.seed_end, sg.col0, sg.cnt};
+            nw_here = std::max(nw_here, sg.col0 + sg.cnt);
+        }
+        for (int32_t col = nw_here; col < B; ++col) ho[col] = -1;
+        // one key and consecutive trial blocks: the key goes in the launch parameters
+        bool uniform = one_key;
+        for (int32_t col = 1; col < nw_here && uniform; ++col) uniform = hg[col] == hg[0] + 16ull * col;
+        pinfo[pass] = PassInfo{nw_here, !uniform, items[ps[0].item].key, hg[0]};
+    }
+    CND_CUDA_TRY(cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(uint64_t) * h_desc.size(), cudaMemcpyHostToDevice, st));
+    // launch parameters of pass i's kernels
+    auto pass_params = [&](size_t pass, Params q) {
+        uint64_t *dv = d_desc + pass * desc_words;
+        q.valid = dv;
+        q.wg0 = dv + B;
+        q.wkey = (const uint2 *)(dv + 3 * (size_t)B);
+        q.rk = round_keys(pinfo[pass].key);
+        q.g_base = pinfo[pass].g_base;
+        q.nvalid = pinfo[pass].nw_here;
+        return q;
+    };
+    auto pass_wout = [&](size_t pass) { return (const int64_t *)(d_desc + pass * desc_words + 2 * (size_t)B); };
+    auto pass_witem = [&](size_t pass) { return (const int32_t *)(d_desc + pass * desc_words + 4 * (size_t)B); };
+    auto pass_segs = [&](size_t pass) {
+        return (const SeedSeg *)(d_desc + pass * desc_words + 4 * (size_t)B + (size_t)(B + 1) / 2);
+    };
 
     P.tau = o.defer_bits;
     P.max_wait = o.defer_steps;
@@ -1086,38 +1225,15 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     int64_t launches = 0;
     const auto t0 = std::chrono::steady_clock::now();
 
-    for (size_t pass = 0; pass < passes.size(); ++pass) {
+    const bool graph_mode = o.graph != 0 && !timing;
+    for (size_t pass = 0; pass < passes.size() && !graph_mode; ++pass) {
         const std::vector<Seg> &ps = passes[pass];
-        std::fill(h_desc.begin(), h_desc.end(), 0ull);
-        bool one_key = true;
-        int32_t nw_here = 0;
-        for (size_t r = 0; r < ps.size(); ++r) {
-            const Seg &sg = ps[r];
-            const ItemDesc &it = items[sg.item];
-            one_key = one_key && it.key == items[ps[0].item].key;
-            for (int32_t c = 0; c < sg.cnt; ++c) {
-                const int32_t col = sg.col0 + c;
-                const int64_t lw = sg.lw0 + c;
-                const int64_t left = it.trials - 64 * lw;
-                h_valid[col] = left >= 64 ? ~0ull : ((1ull << left) - 1ull);
-                h_wg0[col] = (uint64_t)(o.first_trial + 64 * lw) >> 2;
-                h_wout[col] = it.out0 + 64 * lw;
-                h_wkey[col] = make_uint2((uint32_t)it.key, (uint32_t)(it.key >> 32));
-                h_witem[col] = sg.item;
-            }
-            h_segs[r] = SeedSeg{(int32_t)it.seed_begin, (int32_t)it.seed_end, sg.col0, sg.cnt};
-            nw_here = std::max(nw_here, sg.col0 + sg.cnt);
-        }
-        for (int32_t col = nw_here; col < B; ++col) h_wout[col] = -1;
-        // one key and consecutive trial blocks: the key goes in the launch parameters
-        bool uniform = one_key;
-        for (int32_t col = 1; col < nw_here && uniform; ++col) uniform = h_wg0[col] == h_wg0[0] + 16ull * col;
-        const bool pw = !uniform;
-        P.rk = round_keys(items[ps[0].item].key);
-        P.g_base = h_wg0[0];
-        P.nvalid = nw_here;
-        CND_CUDA_TRY(
-            cudaMemcpyAsync(d_desc, h_desc.data(), sizeof(uint64_t) * desc_words, cudaMemcpyHostToDevice, st));
+        P = pass_params(pass, P);
+        const int32_t nw_here = pinfo[pass].nw_here;
+        const bool pw = pinfo[pass].perword;
+        const int64_t *d_wout = pass_wout(pass);
+        const int32_t *d_witem = pass_witem(pass);
+        const SeedSeg *d_segs = pass_segs(pass);
         CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
         if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
         if (model == 1) {
@@ -1226,6 +1342,123 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
                                                                 d_count, d_checks);
         CND_CUDA_TRY(cudaGetLastError());
         launches += 2;
+    }
+    if (graph_mode) {
+        // ---- the whole run as one CUDA graph: per pass its set-up, the seed
+        // step, a WHILE node over the steps (condition set on the device by
+        // k_ctl) and its outputs; one launch
+        Ctl *d_ctl = nullptr;
+        CND_CUDA_TRY(W.alloc(&d_ctl, 1));
+        CND_CUDA_TRY(cudaMemsetAsync(d_ctl, 0, sizeof(Ctl), st));
+        P.ctl = d_ctl;
+        P.fr[0] = fr[0];
+        P.fr[1] = fr[1];
+        P.lists[0] = lists[0];
+        P.lists[1] = lists[1];
+        P.lcnt = d_lcnt;
+        struct Graph {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t x = nullptr;
+            cudaStream_t cs = nullptr;
+            ~Graph() {
+                if (x) cudaGraphExecDestroy(x);
+                if (g) cudaGraphDestroy(g);
+                if (cs) cudaStreamDestroy(cs);
+            }
+        } gr;
+        CND_CUDA_TRY(cudaStreamCreateWithFlags(&gr.cs, cudaStreamNonBlocking));
+        CND_CUDA_TRY(cudaGraphCreate(&gr.g, 0));
+        cudaStream_t cs = gr.cs;
+        std::vector<cudaGraphNode_t> tail;
+        auto cap_begin = [&](cudaGraph_t target, const std::vector<cudaGraphNode_t> &deps) -> cudaError_t {
+            return cudaStreamBeginCaptureToGraph(cs, target, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
+                                                 cudaStreamCaptureModeRelaxed);
+        };
+        auto cap_end = [&](std::vector<cudaGraphNode_t> *tail_out) -> cudaError_t {
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t nd = 0;
+            cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &nd);
+            if (e != cudaSuccess) return e;
+            if (tail_out) tail_out->assign(deps, deps + nd);
+            cudaGraph_t gout = nullptr;
+            return cudaStreamEndCapture(cs, &gout);
+        };
+        const int body_kernels = (may_pull ? 3 : 0) + 3;
+        for (size_t pass = 0; pass < passes.size(); ++pass) {
+            const std::vector<Seg> &ps = passes[pass];
+            Params Q = pass_params(pass, P);
+            const bool pw = pinfo[pass].perword;
+            const int32_t nw_here = pinfo[pass].nw_here;
+            cudaGraphConditionalHandle h;
+            CND_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, gr.g, 0, 0));
+            // set-up and seed step
+            CND_CUDA_TRY(cap_begin(gr.g, tail));
+            CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, cs));
+            if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, cs));
+            if (model == 1) {
+                CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, cs));
+                CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, cs));
+            }
+            CND_CUDA_TRY(cudaMemsetAsync(fr[0].cnt, 0, 4 * sizeof(int32_t), cs));
+            CND_CUDA_TRY(cudaMemsetAsync(d_lcnt, 0, 2 * sizeof(int32_t), cs));
+            k_pass_begin<<<1, 1, 0, cs>>>(Q);
+            k_seed<<<std::max<int>(1, (int)ps.size()), 128, 0, cs>>>(Q, pass_segs(pass), (int32_t)ps.size(),
+                                                                      seeds_dev, d_bad);
+            CND_CUDA_TRY(launch(k_seedfin, seed_blocks, cs, Q));
+            k_ctl<<<1, 1, 0, cs>>>(Q, h, 1, o.max_levels, may_pull ? 1 : 0, o.direction == CND_DIR_PULL ? 1 : 0,
+                                   permille, (int64_t)G.m, P.tau);
+            CND_CUDA_TRY(cudaGetLastError());
+            CND_CUDA_TRY(cap_end(&tail));
+            // the step loop
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t loop_node;
+            CND_CUDA_TRY(cudaGraphAddNode(&loop_node, gr.g, tail.data(), nullptr, tail.size(), &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            CND_CUDA_TRY(cap_begin(body, {}));
+            if (may_pull) {
+                CND_CUDA_TRY(launch((const void *)k_frontier_dense<true>, dense_blocks, cs, Q));
+                CND_CUDA_TRY(launch(pw ? k_pull_pw : k_pull_uk, pull_blocks, cs, Q));
+                CND_CUDA_TRY(launch((const void *)k_frontier_dense<false>, dense_blocks, cs, Q));
+            }
+            CND_CUDA_TRY(launch(pw ? k_push_pw : k_push_uk, push_blocks, cs, Q));
+            CND_CUDA_TRY(launch(pw ? k_fin_pw : k_fin_uk, fin_blocks, cs, Q));
+            k_ctl<<<1, 1, 0, cs>>>(Q, h, 0, o.max_levels, may_pull ? 1 : 0, o.direction == CND_DIR_PULL ? 1 : 0,
+                                   permille, (int64_t)G.m, P.tau);
+            CND_CUDA_TRY(cudaGetLastError());
+            CND_CUDA_TRY(cap_end(nullptr));
+            tail.assign(1, loop_node);
+            // outputs of the pass
+            CND_CUDA_TRY(cap_begin(gr.g, tail));
+            const int npb = 4096;
+            dim3 grid((unsigned)((nw_here + 7) / 8), (unsigned)((n + npb - 1) / npb));
+            k_spread<<<grid, 256, 0, cs>>>(P.vis, n, B, nw_here, npb, pass_wout(pass), d_spread);
+            k_counts<<<blocks_for(n, G.num_sms * 8), 256, 0, cs>>>(P.vis, n, B, G.row_ptr,
+                                                                    batched ? pass_witem(pass) : nullptr, d_count,
+                                                                    d_checks);
+            CND_CUDA_TRY(cudaGetLastError());
+            CND_CUDA_TRY(cap_end(&tail));
+            launches += 6;
+        }
+        CND_CUDA_TRY(cudaGraphInstantiate(&gr.x, gr.g, 0));
+        CND_CUDA_TRY(cudaGraphLaunch(gr.x, st));
+        Ctl hc;
+        CND_CUDA_TRY(cudaMemcpyAsync(&hc, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
+        CND_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hc.limit) limit_hit = true;
+        launches += (int64_t)hc.levels * body_kernels;
+        if (S) {
+            S->levels = (int32_t)hc.levels;
+            S->frontier_slots = (int64_t)hc.slots;
+            S->work_items = (int64_t)hc.items;
+            S->pull_steps = (int64_t)hc.pull_steps;
+            S->expand_launches = (int64_t)hc.levels;
+            S->finalize_launches = (int64_t)hc.levels;
+        }
     }
     if (S) S->launches = launches;
     if (d_ctr) {

@@ -320,3 +320,34 @@ def test_pull_direction_batch_and_edge_cases(rmat14):
     G2 = P.cnd_graph_create(g2.n, g2.row_ptr, g2.col, p2, None)
     for seeds2 in ([0], [9], [0, 0, 3, 3], list(range(10))):
         assert_same(sim("ic", G2, seeds2, 300, 5, direction="pull"), ref("ic", g2, seeds2, 300, 5, p=p2))
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_graph_mode_same_results(ba, rmat14, model):
+    """One CUDA-graph launch per call (device-side step loop) gives the host-loop results."""
+    for fx in (ba, rmat14):
+        g, G, p, w, seeds = fx
+        b = ref(model, g, seeds, 700, 12, p=p, w=w)
+        assert_same(sim(model, G, seeds, 700, 12, graph=1), b)
+        assert_same(sim(model, G, seeds, 700, 12, graph=1, word_bits=192), b)  # several passes
+        a = sim(model, G, seeds, 700, 12, graph=1, stats=2)
+        assert a.stats["levels"] > 0 and a.stats["frontier_slots"] > 0
+        bc = ref(model, g, seeds, 200, 12, p=p, w=w, max_levels=3)
+        assert_same(sim(model, G, seeds, 200, 12, graph=1, max_levels=3), bc)
+    g, G, p, w, seeds = rmat14
+    b0 = ref(model, g, seeds, 256, 2, p=p, w=w, level_counts_len=0)
+    a = sim(model, G, seeds, 256, 2, graph=1, defer_bits=16, defer_steps=2, level_counts_len=0)
+    assert np.array_equal(a.spread, b0.spread) and np.array_equal(a.node_count, b0.node_count)
+    if model == "ic":
+        assert_same(sim("ic", G, seeds, 256, 2, graph=1, direction="pull"), ref("ic", g, seeds, 256, 2, p=p))
+
+
+def test_graph_mode_batch(rmat14):
+    g, G, p, w, _ = rmat14
+    seed_off, seeds, trials, keys = I.batch_items(g.n, 17, 1, 40, (64, 256, 1000, 3), graph_seed=9)
+    for model in ("ic", "lt"):
+        f = P.cnd_ic_simulate_batch if model == "ic" else P.cnd_lt_simulate_batch
+        want_sp, want_nc, want_ck = _batch_ref(model, g, p, w, seed_off, seeds, trials, keys)
+        a = f(G, seed_off, seeds, trials, keys, node_count=True, edge_checks=True, graph=1, word_bits=256)
+        assert np.array_equal(a.spread, want_sp) and np.array_equal(a.node_count, want_nc)
+        assert a.edge_checks == want_ck
