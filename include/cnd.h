@@ -138,7 +138,11 @@ typedef struct cnd_sim_opts {
                                   and its step loop (a device-side WHILE node whose condition a
                                   one-thread control kernel sets after each step), no host round
                                   trip per step; ignored with CND_STATS_TIMING */
-    int64_t reserved[2];
+    int32_t autotune;          /* 1: take word_bits, chunk_edges, pull_permille and graph from the
+                                  autotuner's cache for this graph, model and problem size class,
+                                  tuning (cnd_autotune on a sample of this call) on a miss */
+    int32_t reserved2;
+    int64_t reserved[1];
 } cnd_sim_opts;
 
 void cnd_sim_opts_init(cnd_sim_opts *opts);
@@ -214,6 +218,25 @@ cnd_status cnd_ic_simulate_batch(const cnd_graph *g, int32_t n_items, const int6
 cnd_status cnd_lt_simulate_batch(const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,
                                  const int32_t *n_trials, const uint64_t *rng_seed, int32_t *spread_out,
                                  int32_t *node_count_out, const cnd_sim_opts *opts);
+
+/*
+ * Autotuner: times candidate settings of the engine on a sample of the given
+ * work (at most 4,096 trials of a single seed set, or the first 4 items of a
+ * batch with at most 512 trials each) and writes the fastest into *best_out
+ * (a copy of *base with word_bits, chunk_edges, pull_permille and graph set).
+ * The candidates: pass widths of 256, 64 and 16 words (single seed sets; the
+ * widest for batches); 0 (by frontier words),
+ * 32 and 512 edges per work item; push only or pull above 25 % of m (IC);
+ * host loop or one CUDA graph per call.  The result is cached per (graph,
+ * model, single or batch, log2 trials, log2 seeds) for opts.autotune.
+ * model: 0 IC, 1 LT.  Single seed set: n_items = 0, seed_off NULL, n_trials[0]
+ * and rng_seed[0] describe it.  Arrays as in the simulate calls; best_ms_out
+ * (may be NULL) receives the sample time of the winner in milliseconds.
+ * Every candidate computes the same results, so tuning never changes outputs.
+ */
+cnd_status cnd_autotune(const cnd_graph *g, int32_t model, int32_t n_items, const int64_t *seed_off,
+                        const int32_t *seeds, int32_t n_seeds, const int32_t *n_trials, const uint64_t *rng_seed,
+                        const cnd_sim_opts *base, cnd_sim_opts *best_out, double *best_ms_out);
 
 /*
  * Weighted-cascade LT weights for a CSR graph (Sec. 4 "Benchmarks", WC model:

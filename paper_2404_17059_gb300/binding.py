@@ -25,7 +25,7 @@ EXPORTS = (
     "cnd_sim_opts_init", "cnd_graph_create", "cnd_graph_destroy", "cnd_graph_info", "cnd_ic_simulate",
     "cnd_lt_simulate", "cnd_ic_simulate_ex", "cnd_lt_simulate_ex", "cnd_lt_weights_wc",
     "cnd_philox4x32_10", "cnd_last_error", "cnd_ic_simulate_noalloc", "cnd_ic_simulate_batch",
-    "cnd_lt_simulate_batch",
+    "cnd_lt_simulate_batch", "cnd_autotune",
 )
 
 
@@ -81,7 +81,9 @@ class cnd_sim_opts(C.Structure):
         ("stats", C.c_void_p),
         ("defer_steps", C.c_int32),
         ("graph", C.c_int32),
-        ("reserved", C.c_int64 * 2),
+        ("autotune", C.c_int32),
+        ("reserved2", C.c_int32),
+        ("reserved", C.c_int64 * 1),
     ]
 
 
@@ -123,6 +125,9 @@ def load(build_if_missing: bool = True):
         for name in ("cnd_ic_simulate_batch", "cnd_lt_simulate_batch"):
             getattr(L, name).argtypes = [vp, i32, vp, vp, vp, vp, vp, vp, C.POINTER(cnd_sim_opts)]
             getattr(L, name).restype = i32
+        L.cnd_autotune.argtypes = [vp, i32, i32, vp, vp, i32, vp, vp, C.POINTER(cnd_sim_opts),
+                                   C.POINTER(cnd_sim_opts), C.POINTER(C.c_double)]
+        L.cnd_autotune.restype = i32
         L.cnd_lt_weights_wc.argtypes = [i32, i32, vp, vp]
         L.cnd_lt_weights_wc.restype = i32
         L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
@@ -214,7 +219,7 @@ class SimResult:
 def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=True, node_count=True,
               first_trial=0, max_levels=0, direction="auto", word_bits=0, level_counts_len=0,
               edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None, stats=0,
-              defer_bits=0, defer_steps=0, graph=0):
+              defer_bits=0, defer_steps=0, graph=0, autotune=0):
     L = load()
     n_trials = int(n_trials)
     dev = _is_torch_cuda(seeds)
@@ -261,6 +266,7 @@ def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=Tru
         o.defer_bits = int(defer_bits)
         o.defer_steps = int(defer_steps)
         o.graph = int(graph)
+        o.autotune = int(autotune)
         o.timeout_s = float(timeout_s)
         stt = None
         if stats:
@@ -395,3 +401,24 @@ def cnd_ic_simulate_batch(g, seed_off, seeds, n_trials, rng_seed, **kw) -> SimRe
 
 def cnd_lt_simulate_batch(g, seed_off, seeds, n_trials, rng_seed, **kw) -> SimResult:
     return _simulate_batch("cnd_lt_simulate_batch", g, seed_off, seeds, n_trials, rng_seed, **kw)
+
+
+def cnd_autotune(g, model, seeds, n_trials, rng_seed, *, seed_off=None) -> dict:
+    """Autotuner: the fastest engine settings for this work (host arrays).
+
+    Single seed set: ``seeds``, ``n_trials`` and ``rng_seed`` are scalars / one
+    array; batch: pass ``seed_off`` and per-item ``n_trials`` / ``rng_seed``."""
+    L = load()
+    mdl = {"ic": 0, "lt": 1}[model] if isinstance(model, str) else int(model)
+    seeds = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).ravel())
+    tr = np.ascontiguousarray(np.atleast_1d(np.asarray(n_trials, dtype=np.int32)))
+    ks = np.ascontiguousarray(np.atleast_1d(np.asarray(rng_seed, dtype=np.uint64)))
+    so = None if seed_off is None else np.ascontiguousarray(seed_off, dtype=np.int64)
+    n_items = 0 if so is None else int(tr.shape[0])
+    best = cnd_sim_opts()
+    ms = C.c_double()
+    base = cnd_sim_opts_init()
+    _check(L.cnd_autotune(g.handle, mdl, n_items, _np_ptr(so), _np_ptr(seeds) if seeds.size else None,
+                          int(seeds.size), _np_ptr(tr), _np_ptr(ks), C.byref(base), C.byref(best), C.byref(ms)))
+    return {"word_bits": best.word_bits, "chunk_edges": best.chunk_edges, "pull_permille": best.pull_permille,
+            "graph": best.graph, "sample_ms": ms.value}

@@ -37,7 +37,9 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "cnd_common.cuh"
@@ -1476,6 +1478,142 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     return CND_OK;
 }
 
+// ---------------------------------------------------------------- autotuner
+struct TuneVal {
+    int32_t word_bits, chunk_edges, pull_permille, graph;
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<const void *, int, int, int, int>, TuneVal> g_tune_cache;
+
+static int log2_bucket(int64_t x) {
+    int b = 0;
+    while (x > 1) {
+        x >>= 1;
+        ++b;
+    }
+    return b;
+}
+
+static cnd_status simulate_common(int model, const cnd_graph *g, const char *fn, int32_t n_items,
+                                  const int64_t *seed_off, const int32_t *seeds, const int32_t *n_trials_arr,
+                                  int64_t n_trials_one, const uint64_t *keys, uint64_t key_one, int32_t *spread_out,
+                                  int32_t *count_out, const cnd_sim_opts *opts);
+
+// Times the candidates on a sample; returns the best settings.
+static cnd_status tune(int model, const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,
+                       const int32_t *n_trials_arr, int64_t n_trials_one, const uint64_t *keys, uint64_t key_one,
+                       bool batched, const cnd_sim_opts &base, TuneVal &best, double &best_ms) {
+    // the sample: its own copies of the (small) item metadata
+    int32_t ns_items = batched ? std::min(n_items, 4) : 1;
+    std::vector<int32_t> tr((size_t)ns_items);
+    int64_t total = 0;
+    for (int32_t i = 0; i < ns_items; ++i) {
+        tr[i] = batched ? std::min<int32_t>(n_trials_arr[i], 512) : (int32_t)std::min<int64_t>(n_trials_one, 4096);
+        total += tr[i];
+    }
+    if (total == 0) {
+        best = TuneVal{0, 0, 0, 0};
+        best_ms = 0.0;
+        return CND_OK;
+    }
+    const int64_t total_words = batched ? 0 : (total + 63) / 64;
+    std::vector<int32_t> widths = {0};  // 0 = widest pass that fits
+    for (int wb : {64 * 64, 16 * 64})
+        if (!batched && wb < 64 * total_words) widths.push_back(wb);
+    const std::vector<int32_t> chunks = {0, 32, 512};
+    std::vector<int32_t> pulls = {0};
+    if (model == 0) pulls.push_back(250);
+    cnd_sim_opts o = base;
+    o.autotune = 0;
+    o.stats = nullptr;
+    o.edge_checks_out = nullptr;
+    o.level_counts_out = nullptr;
+    o.level_counts_len = 0;
+    o.max_levels = 0;
+    o.direction = CND_DIR_AUTO;
+    const bool dev = o.device_ptrs != 0;
+    // outputs of the sample runs
+    int32_t *d_sp = nullptr;
+    std::vector<int32_t> h_sp;
+    if (dev) {
+        if (cudaMalloc(&d_sp, sizeof(int32_t) * (size_t)total) != cudaSuccess) {
+            set_error("cnd_autotune: allocation failed");
+            return CND_ENOMEM;
+        }
+    } else {
+        h_sp.resize((size_t)total);
+    }
+    int32_t *sp = dev ? d_sp : h_sp.data();
+    best_ms = 1e300;
+    // one untimed run first (first-call costs: pool growth, module load)
+    cnd_status st = simulate_common(model, g, "cnd_autotune", batched ? ns_items : 1, seed_off, seeds,
+                                    batched ? tr.data() : nullptr, batched ? 0 : tr[0], keys, key_one, sp, nullptr, &o);
+    for (int32_t wb : widths)
+        for (int32_t ch : chunks)
+            for (int32_t pm : pulls)
+                for (int32_t gr : {0, 1}) {
+                    o.word_bits = wb;
+                    o.chunk_edges = ch;
+                    o.pull_permille = pm;
+                    o.graph = gr;
+                    double t_best = 1e300;
+                    for (int rep = 0; rep < 1 && st == CND_OK; ++rep) {
+                        const auto t0 = std::chrono::steady_clock::now();
+                        st = simulate_common(model, g, "cnd_autotune", batched ? ns_items : 1, seed_off, seeds,
+                                             batched ? tr.data() : nullptr, batched ? 0 : tr[0], keys, key_one, sp,
+                                             nullptr, &o);
+                        if (st == CND_OK && dev) st = cudaStreamSynchronize((cudaStream_t)o.stream) == cudaSuccess
+                                                          ? CND_OK
+                                                          : CND_ECUDA;
+                        const double ms =
+                            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+                        t_best = std::min(t_best, ms);
+                    }
+                    if (st != CND_OK) break;
+                    if (t_best < best_ms) {
+                        best_ms = t_best;
+                        best = TuneVal{wb, ch, pm, gr};
+                    }
+                }
+    if (d_sp) cudaFree(d_sp);
+    return st;
+}
+
+static cnd_status apply_autotune(int model, const cnd_graph *g, int32_t n_items, const int64_t *seed_off,
+                                 const int32_t *seeds, const int32_t *n_trials_arr, int64_t n_trials_one,
+                                 const uint64_t *keys, uint64_t key_one, bool batched, cnd_sim_opts &o) {
+    int64_t total = 0, n_seeds = 0;
+    for (int32_t i = 0; i < (batched ? n_items : 1); ++i) {
+        total += batched ? n_trials_arr[i] : n_trials_one;
+        n_seeds += batched ? seed_off[i + 1] - seed_off[i] : seed_off[1];
+    }
+    const auto key = std::make_tuple((const void *)g, model, batched ? 1 : 0, log2_bucket(total),
+                                     log2_bucket(std::max<int64_t>(1, n_seeds / std::max(1, batched ? n_items : 1))));
+    TuneVal tv{};
+    bool hit = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            tv = it->second;
+            hit = true;
+        }
+    }
+    if (!hit) {
+        double ms = 0.0;
+        const cnd_status st =
+            tune(model, g, n_items, seed_off, seeds, n_trials_arr, n_trials_one, keys, key_one, batched, o, tv, ms);
+        if (st != CND_OK) return st;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = tv;
+    }
+    o.word_bits = tv.word_bits;
+    o.chunk_edges = tv.chunk_edges;
+    o.pull_permille = tv.pull_permille;
+    o.graph = tv.graph;
+    return CND_OK;
+}
+
 // Shared front end of the single and batched entry points.
 static cnd_status simulate_common(int model, const cnd_graph *g, const char *fn, int32_t n_items,
                                   const int64_t *seed_off, const int32_t *seeds, const int32_t *n_trials_arr,
@@ -1507,6 +1645,12 @@ static cnd_status simulate_common(int model, const cnd_graph *g, const char *fn,
     if (o.defer_bits > 0 && (o.level_counts_len > 0 || o.max_levels > 0)) {
         set_error("%s: defer_bits changes activation steps; it cannot be combined with level counts or max_levels", fn);
         return CND_EINVAL;
+    }
+    if (o.autotune) {
+        const cnd_status ts = apply_autotune(model, g, n_items, seed_off, seeds, n_trials_arr, n_trials_one, keys,
+                                             key_one, batched, o);
+        if (ts != CND_OK) return ts;
+        o.autotune = 0;
     }
     // ---- items
     std::vector<ItemDesc> items((size_t)n_items);
@@ -1686,6 +1830,36 @@ cnd_status cnd_lt_simulate_ex(const cnd_graph *g, const int32_t *seeds, int32_t 
                               uint64_t rng_seed, int32_t *spread_out, int32_t *node_count_out,
                               const cnd_sim_opts *opts) {
     return simulate(1, g, seeds, n_seeds, n_trials, rng_seed, spread_out, node_count_out, opts);
+}
+
+cnd_status cnd_autotune(const cnd_graph *g, int32_t model, int32_t n_items, const int64_t *seed_off,
+                        const int32_t *seeds, int32_t n_seeds, const int32_t *n_trials, const uint64_t *rng_seed,
+                        const cnd_sim_opts *base, cnd_sim_opts *best_out, double *best_ms_out) {
+    clear_error();
+    if (!g || (model != 0 && model != 1) || n_items < 0 || !n_trials || !rng_seed || !best_out ||
+        (n_items > 0 && !seed_off) || (n_items == 0 && n_seeds < 0)) {
+        set_error("cnd_autotune: bad arguments");
+        return CND_EINVAL;
+    }
+    cnd_sim_opts o;
+    cnd_sim_opts_init(&o);
+    if (base) o = *base;
+    const bool batched = n_items > 0;
+    const int64_t off1[2] = {0, n_seeds};
+    TuneVal tv{};
+    double ms = 0.0;
+    const cnd_status st = tune(model, g, batched ? n_items : 1, batched ? seed_off : off1, seeds,
+                               batched ? n_trials : nullptr, batched ? 0 : n_trials[0], rng_seed,
+                               batched ? 0 : rng_seed[0], batched, o, tv, ms);
+    if (st != CND_OK) return st;
+    o.word_bits = tv.word_bits;
+    o.chunk_edges = tv.chunk_edges;
+    o.pull_permille = tv.pull_permille;
+    o.graph = tv.graph;
+    o.autotune = 0;
+    *best_out = o;
+    if (best_ms_out) *best_ms_out = ms;
+    return CND_OK;
 }
 
 cnd_status cnd_ic_simulate_batch(const cnd_graph *g, int32_t n_items, const int64_t *seed_off, const int32_t *seeds,

@@ -351,3 +351,23 @@ def test_graph_mode_batch(rmat14):
         a = f(G, seed_off, seeds, trials, keys, node_count=True, edge_checks=True, graph=1, word_bits=256)
         assert np.array_equal(a.spread, want_sp) and np.array_equal(a.node_count, want_nc)
         assert a.edge_checks == want_ck
+
+
+def test_autotune_keeps_results(ba, rmat14):
+    """The autotuner only picks engine settings: results stay bit-exact."""
+    g, G, p, w, seeds = ba
+    best = P.cnd_autotune(G, "ic", seeds, 3000, 1)
+    assert best["word_bits"] in (0, 1024, 4096) and best["chunk_edges"] in (0, 32, 512)
+    assert best["graph"] in (0, 1) and best["sample_ms"] > 0
+    b = ref("ic", g, seeds, 3000, 1, p=p, level_counts_len=0)
+    for _ in range(2):  # tunes on the first call, cache hit on the second
+        a = sim("ic", G, seeds, 3000, 1, autotune=1, level_counts_len=0)
+        assert np.array_equal(a.spread, b.spread) and np.array_equal(a.node_count, b.node_count)
+        assert a.edge_checks == b.edge_checks
+    g, G, p, w, _ = rmat14
+    seed_off, seeds2, trials, keys = I.batch_items(g.n, 12, 1, 30, (64, 300), graph_seed=10)
+    best = P.cnd_autotune(G, "lt", seeds2, trials, keys, seed_off=seed_off)
+    assert best["pull_permille"] == 0
+    want_sp, want_nc, want_ck = _batch_ref("lt", g, p, w, seed_off, seeds2, trials, keys)
+    a = P.cnd_lt_simulate_batch(G, seed_off, seeds2, trials, keys, edge_checks=True, autotune=1)
+    assert np.array_equal(a.spread, want_sp) and a.edge_checks == want_ck
