@@ -164,10 +164,13 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+ENGINE_SOURCES = ("cnd_common.cuh", "cnd_sim.cu")  # the expansion kernels the traffic figures cover
+
+
 def source_hash() -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2404_17059_gb300", "csrc")
-    for fn in sorted(os.listdir(d)):
+    for fn in ENGINE_SOURCES:
         with open(os.path.join(d, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
