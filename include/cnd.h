@@ -239,6 +239,58 @@ cnd_status cnd_autotune(const cnd_graph *g, int32_t model, int32_t n_items, cons
                         const cnd_sim_opts *base, cnd_sim_opts *best_out, double *best_ms_out);
 
 /*
+ * Influence maximisation by lazy greedy (CELF, Leskovec et al. 2007) on the
+ * batched engine (Sec. 2 "Influence Maximization": choose |S| = k maximising
+ * sigma(S); the paper applies CELF in Sec. 4 "Influence Maximization").
+ *
+ * sigma is estimated with common random numbers: every evaluation of a set X
+ * runs trials first_trial .. first_trial + n_trials - 1 of key rng_seed, and
+ * the value used is the exact integer F(X) = sum over those trials of the
+ * spread.  For IC, F is a coverage function of the trials' live-edge graphs,
+ * hence submodular, and the result equals plain greedy's.  The rule, which
+ * fixes the result for both models:
+ *   round 0: gain(v) = F({v}) for every candidate (a candidate with no
+ *            out-edges has F({v}) = n_trials without simulation);
+ *   round j: entries are ordered by (gain descending, node id ascending);
+ *            while the first entry was last evaluated before round j, the
+ *            stale entries that precede the first fresh one (at most
+ *            eval_batch of them, in order) are re-evaluated in one batched
+ *            call, gain(v) = F(S + v) - F(S); the first entry, once fresh, is
+ *            chosen and F(S) grows by its gain.
+ *   k:              seeds to choose, 1 <= k <= number of candidates.
+ *   n_trials:       trials per evaluation, 1 .. 2^31 - 1.
+ *   candidates:     host array of n_candidates distinct node ids, or NULL for
+ *                   all nodes (n_candidates ignored).
+ *   eval_batch:     0 = 64.  max_items: items per batched call, 0 = 8192.
+ *   sim:            engine settings for the batched calls (NULL = defaults;
+ *                   its first_trial is used, device_ptrs, stream and output
+ *                   pointers are ignored).
+ *   stream:         cudaStream_t for the work (NULL = legacy default stream).
+ * Outputs (host): seeds_out[j] = j-th chosen node; f_out (may be NULL)[j] =
+ * F(first j+1 seeds) (sigma estimate = f_out[j] / n_trials); evaluations_out
+ * and edge_checks_out (may be NULL) count the sets simulated and their edge
+ * checks.  Returns when the results are written.
+ */
+typedef struct {
+    int32_t k;
+    int32_t eval_batch;
+    int64_t n_trials;
+    uint64_t rng_seed;
+    const int32_t *candidates;
+    int32_t n_candidates;
+    int32_t max_items;
+    const cnd_sim_opts *sim;
+    void *stream;
+    int64_t *evaluations_out;
+    int64_t *edge_checks_out;
+    int64_t reserved[4];
+} cnd_im_opts;
+
+void cnd_im_opts_init(cnd_im_opts *o);
+cnd_status cnd_ic_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *seeds_out, int64_t *f_out);
+cnd_status cnd_lt_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *seeds_out, int64_t *f_out);
+
+/*
  * Weighted-cascade LT weights for a CSR graph (Sec. 4 "Benchmarks", WC model:
  * the weight of every edge entering v is 1/in-degree(v)) in fixed point:
  * w_out[e] = floor((2^32 - 1) / in-degree(col[e])), so in-weights sum to at

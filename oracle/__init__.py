@@ -12,3 +12,4 @@ from .oracle import (  # noqa: F401
     build, lib, philox, ic_coin, lt_theta, ic_threshold, simulate, simulate_threads,
     OracleResult, OK, LIMIT, EINVAL, EOVERFLOW,
 )
+from . import im  # noqa: F401  (lazy-greedy influence maximisation on the oracle)

@@ -6,6 +6,6 @@
 from .binding import (  # noqa: F401
     CndError, CndGraph, SimResult, cnd_graph_create, cnd_graph_destroy, cnd_graph_info, cnd_ic_simulate,
     cnd_lt_simulate, cnd_ic_simulate_ex, cnd_lt_simulate_ex, cnd_lt_weights_wc, cnd_philox4x32_10,
-    cnd_last_error, cnd_sim_opts_init, cnd_ic_simulate_noalloc, cnd_ic_simulate_batch, cnd_lt_simulate_batch, cnd_autotune, CND_OK, CND_EINVAL, CND_ENOMEM, CND_ECUDA, CND_ELIMIT, CND_ETIMEOUT,
+    cnd_last_error, cnd_sim_opts_init, cnd_ic_simulate_noalloc, cnd_ic_simulate_batch, cnd_lt_simulate_batch, cnd_autotune, cnd_ic_im_celf, cnd_lt_im_celf, ImResult, CND_OK, CND_EINVAL, CND_ENOMEM, CND_ECUDA, CND_ELIMIT, CND_ETIMEOUT,
     CND_EOVERFLOW,
 )

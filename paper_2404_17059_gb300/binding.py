@@ -25,7 +25,7 @@ EXPORTS = (
     "cnd_sim_opts_init", "cnd_graph_create", "cnd_graph_destroy", "cnd_graph_info", "cnd_ic_simulate",
     "cnd_lt_simulate", "cnd_ic_simulate_ex", "cnd_lt_simulate_ex", "cnd_lt_weights_wc",
     "cnd_philox4x32_10", "cnd_last_error", "cnd_ic_simulate_noalloc", "cnd_ic_simulate_batch",
-    "cnd_lt_simulate_batch", "cnd_autotune",
+    "cnd_lt_simulate_batch", "cnd_autotune", "cnd_im_opts_init", "cnd_ic_im_celf", "cnd_lt_im_celf",
 )
 
 
@@ -91,6 +91,15 @@ _lock = threading.Lock()
 _lib = None
 
 
+class cnd_im_opts(C.Structure):
+    _fields_ = [
+        ("k", C.c_int32), ("eval_batch", C.c_int32), ("n_trials", C.c_int64), ("rng_seed", C.c_uint64),
+        ("candidates", C.c_void_p), ("n_candidates", C.c_int32), ("max_items", C.c_int32),
+        ("sim", C.c_void_p), ("stream", C.c_void_p), ("evaluations_out", C.c_void_p),
+        ("edge_checks_out", C.c_void_p), ("reserved", C.c_int64 * 4),
+    ]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -128,6 +137,11 @@ def load(build_if_missing: bool = True):
         L.cnd_autotune.argtypes = [vp, i32, i32, vp, vp, i32, vp, vp, C.POINTER(cnd_sim_opts),
                                    C.POINTER(cnd_sim_opts), C.POINTER(C.c_double)]
         L.cnd_autotune.restype = i32
+        L.cnd_im_opts_init.argtypes = [vp]
+        L.cnd_im_opts_init.restype = None
+        for name in ("cnd_ic_im_celf", "cnd_lt_im_celf"):
+            getattr(L, name).argtypes = [vp, C.POINTER(cnd_im_opts), vp, vp]
+            getattr(L, name).restype = i32
         L.cnd_lt_weights_wc.argtypes = [i32, i32, vp, vp]
         L.cnd_lt_weights_wc.restype = i32
         L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
@@ -422,3 +436,52 @@ def cnd_autotune(g, model, seeds, n_trials, rng_seed, *, seed_off=None) -> dict:
                           int(seeds.size), _np_ptr(tr), _np_ptr(ks), C.byref(base), C.byref(best), C.byref(ms)))
     return {"word_bits": best.word_bits, "chunk_edges": best.chunk_edges, "pull_permille": best.pull_permille,
             "graph": best.graph, "sample_ms": ms.value}
+
+
+@dataclasses.dataclass
+class ImResult:
+    seeds: np.ndarray        # int32 [k], in the order chosen
+    f: np.ndarray            # int64 [k]: F(first j+1 seeds) = sum of spreads over the trials
+    evaluations: int         # seed sets simulated
+    edge_checks: int
+
+
+def _im_celf(fn_name, g, k, n_trials, rng_seed, *, candidates=None, eval_batch=0, max_items=0, first_trial=0,
+             stream=None, **sim_kw) -> ImResult:
+    L = load()
+    o = cnd_im_opts()
+    L.cnd_im_opts_init(C.byref(o))
+    o.k = int(k)
+    o.n_trials = int(n_trials)
+    o.rng_seed = int(rng_seed)
+    o.eval_batch = int(eval_batch)
+    o.max_items = int(max_items)
+    cand = None
+    if candidates is not None:
+        cand = np.ascontiguousarray(np.asarray(candidates, dtype=np.int32).ravel())
+        o.candidates = _np_ptr(cand)
+        o.n_candidates = int(cand.size)
+    so = cnd_sim_opts_init()
+    so.first_trial = int(first_trial)
+    for key, val in sim_kw.items():
+        setattr(so, key, int(val))
+    o.sim = C.cast(C.pointer(so), C.c_void_p)
+    o.stream = stream
+    ev = C.c_int64()
+    ec = C.c_int64()
+    o.evaluations_out = C.cast(C.pointer(ev), C.c_void_p)
+    o.edge_checks_out = C.cast(C.pointer(ec), C.c_void_p)
+    seeds = np.empty(int(k), dtype=np.int32)
+    f = np.empty(int(k), dtype=np.int64)
+    _check(getattr(L, fn_name)(g.handle, C.byref(o), _np_ptr(seeds), _np_ptr(f)))
+    return ImResult(seeds, f, ev.value, ec.value)
+
+
+def cnd_ic_im_celf(g, k, n_trials, rng_seed, **kw) -> ImResult:
+    """Lazy-greedy (CELF) IC influence maximisation; engine options (word_bits, chunk_edges,
+    pull_permille, graph, autotune) pass through to the batched calls."""
+    return _im_celf("cnd_ic_im_celf", g, k, n_trials, rng_seed, **kw)
+
+
+def cnd_lt_im_celf(g, k, n_trials, rng_seed, **kw) -> ImResult:
+    return _im_celf("cnd_lt_im_celf", g, k, n_trials, rng_seed, **kw)
