@@ -17,6 +17,12 @@ ingest happens once, before the timed region):
                     per edge; one batched IC call over the first K of 4,096 seed
                     sets (|S| ~ U{1..100}, trials from {256, 1024, 4096}).
   er1k              directed ER n=1,000, m=10,000, p=0.1, 10 seeds, 1,000 trials.
+  celf_rr7          influence maximisation: CELF with k=10 on a random 7-regular
+                    graph, n=5,000 (35,000 directed edges), IC with trivalency and
+                    weighted-cascade probabilities, 1,000 common trials per
+                    evaluation (--trials); a step is one CELF run per model.
+                    metric: seconds per CELF run (lower is better), next to the
+                    oracle's CELF on the host cores.
 
 value        = edge checks per second over the whole job (all ranks), device-
                resident inputs, CUDA-event time of each step, L2 flushed
@@ -327,6 +333,65 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- CELF
+CELF_K = 10
+
+
+def celf_models(trials):
+    g = I.random_regular(5000, 7, graph_seed=1)
+    return g, {"tv": I.ic_trivalency(g, graph_seed=1), "wc": I.ic_weighted_cascade(g)}, trials or 1000
+
+
+def run_celf(args):
+    """CELF (k=10) on the random 7-regular graph: GPU batch engine vs the oracle's CELF."""
+    import torch
+    import paper_2404_17059_gb300 as P
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    g, probs, T = celf_models(args.trials)
+    res = {}
+    for name, p in probs.items():
+        G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+        for _ in range(args.warmup):
+            r = P.cnd_ic_im_celf(G, CELF_K, T, 1, graph=1)
+        times = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = P.cnd_ic_im_celf(G, CELF_K, T, 1, graph=1)
+            times.append(time.perf_counter() - t0)
+        res[name] = {"s_per_run": statistics.median(times), "runs_s": times, "seeds": r.seeds.tolist(),
+                     "sigma": (r.f / T).tolist(), "evaluations": r.evaluations, "edge_checks": r.edge_checks}
+        P.cnd_graph_destroy(G)
+    cpu = None
+    if not args.no_cpu_baseline and rank == 0:
+        from oracle import im
+        cores = len(os.sched_getaffinity(0))
+        cpu = {}
+        for name, p in probs.items():
+            t0 = time.perf_counter()
+            s_, f_, ev = im.celf("ic", g, CELF_K, T, 1, threads=cores, ic_prob=p)
+            dt = time.perf_counter() - t0
+            same = s_.tolist() == res[name]["seeds"] and (f_ / T).tolist() == res[name]["sigma"]
+            cpu[name] = {"s_per_run": dt, "evaluations": ev, "same_seeds_and_sigma": same}
+        cpu = {"value": sum(v["s_per_run"] for v in cpu.values()), "unit": "s", "cores": cores, "kind": "oracle",
+               "sample": f"the full CELF (k={CELF_K}, {T} trials) per model on {cores} threads", "models": cpu}
+    if rank != 0:
+        return 0
+    total = sum(v["s_per_run"] for v in res.values())
+    line = {"metric": f"CELF k={CELF_K} wall-clock seconds (TV + WC IC)", "value": total, "unit": "s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total,
+            "higher_is_better": False, "scaling": "replicas only", "vs_baseline": None, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": f"random 7-regular n=5000 (35000 directed edges), IC trivalency and weighted "
+                                   f"cascade, CELF k={CELF_K}, {T} common trials per evaluation, rng_seed=1",
+                       "name": "celf_rr7", "timing": "host wall clock around each CELF call (device work synced)"},
+            "models": res, "cpu_baseline": cpu,
+            "paper_context": "CyNetDiff (Cython, one CPU core, trial count unstated): 2 s TV, 10 s WC for CELF k=10"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- our arm
 KERNEL = {"ic": "k_push<0>", "lt": "k_push<1>"}
 
@@ -492,7 +557,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ba100k", choices=["ba100k", "rmat24", "rmat20batch", "er1k"])
+    ap.add_argument("--workload", default="ba100k",
+                    choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trials", type=int, default=0, help="override the workload's trials per model")
     ap.add_argument("--items", type=int, default=0, help="rmat20batch: seed sets per step (default 64)")
@@ -505,6 +571,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "celf_rr7":
+        return run_celf(args)
     return run_ours(args)
 
 

@@ -263,8 +263,9 @@ cnd_status cnd_autotune(const cnd_graph *g, int32_t model, int32_t n_items, cons
  *                   all nodes (n_candidates ignored).
  *   eval_batch:     0 = 64.  max_items: items per batched call, 0 = 8192.
  *   sim:            engine settings for the batched calls (NULL = defaults;
- *                   its first_trial is used, device_ptrs, stream and output
- *                   pointers are ignored).
+ *                   its first_trial, a multiple of 64 as for every batched
+ *                   call, is used; device_ptrs, stream and output pointers
+ *                   are ignored).
  *   stream:         cudaStream_t for the work (NULL = legacy default stream).
  * Outputs (host): seeds_out[j] = j-th chosen node; f_out (may be NULL)[j] =
  * F(first j+1 seeds) (sigma estimate = f_out[j] / n_trials); evaluations_out

@@ -227,27 +227,51 @@ def rmat(scale: int, n_samples: int, a: float = 0.57, b: float = 0.19, c: float 
     return Graph(n=n, row_ptr=row_ptr.astype(np.int32), col=col, name=f"rmat_s{scale}_{n_samples}")
 
 
-def random_regular(n: int, d: int, graph_seed: int = 1, max_tries: int = 1000) -> Graph:
-    """Random d-regular simple undirected graph (pairing model with restarts), both directions stored."""
-    if (n * d) % 2:
-        raise ValueError("n*d must be even")
+def random_regular(n: int, d: int, graph_seed: int = 1, max_tries: int = 100) -> Graph:
+    """Random d-regular simple undirected graph, both directions stored (n*d directed edges).
+
+    Sequential stub pairing in the manner of Steger and Wormald (1999): two
+    random open stubs are joined when that makes neither a self-loop nor a
+    repeated edge; when no such pair is left the attempt restarts.  (Plain
+    pairing with rejection of the whole graph succeeds with probability about
+    exp(-(d^2 - 1) / 4), hopeless beyond d = 4.)
+    """
+    if (n * d) % 2 or d >= n:
+        raise ValueError("need n*d even and d < n")
     rng = _rng(graph_seed)
     for _ in range(max_tries):
         stubs = np.repeat(np.arange(n, dtype=np.int64), d)
         rng.shuffle(stubs)
-        u = stubs[0::2]
-        v = stubs[1::2]
-        if np.any(u == v):
-            continue
-        lo = np.minimum(u, v)
-        hi = np.maximum(u, v)
-        k = lo * n + hi
-        if np.unique(k).size != k.size:
-            continue
-        src = np.concatenate([u, v])
-        dst = np.concatenate([v, u])
-        return csr_from_edges(n, src, dst, name=f"rr_n{n}_d{d}")
-    raise RuntimeError("pairing model did not produce a simple graph")
+        open_ = list(stubs)
+        adj = [set() for _ in range(n)]
+        src, dst = [], []
+        stuck = False
+        while open_ and not stuck:
+            for _attempt in range(64):
+                i, j = rng.integers(0, len(open_), size=2)
+                u, v = open_[i], open_[j]
+                if i != j and u != v and v not in adj[u]:
+                    break
+            else:
+                ok = [(i, j) for i in range(len(open_)) for j in range(i + 1, len(open_))
+                      if open_[i] != open_[j] and open_[j] not in adj[open_[i]]]
+                if not ok:
+                    stuck = True
+                    break
+                i, j = ok[int(rng.integers(0, len(ok)))]
+                u, v = open_[i], open_[j]
+            adj[u].add(v)
+            adj[v].add(u)
+            src.append(u)
+            dst.append(v)
+            for k in sorted((int(i), int(j)), reverse=True):
+                open_[k] = open_[-1]
+                open_.pop()
+        if not stuck:
+            s_ = np.asarray(src, dtype=np.int64)
+            t_ = np.asarray(dst, dtype=np.int64)
+            return csr_from_edges(n, np.concatenate([s_, t_]), np.concatenate([t_, s_]), name=f"rr_n{n}_d{d}")
+    raise RuntimeError("stub pairing kept getting stuck")
 
 
 def watts_strogatz(n: int, k: int, p: float, graph_seed: int = 1) -> Graph:

@@ -34,6 +34,20 @@ def test_opts_struct_layout():
     assert binding.cnd_sim_opts.timeout_s.offset == 64
 
 
+def test_im_opts_layout_and_host_validation():
+    import ctypes
+    assert ctypes.sizeof(binding.cnd_im_opts) == 104
+    assert binding.cnd_im_opts.sim.offset == 40 and binding.cnd_im_opts.reserved.offset == 72
+    L = binding.load()
+    o = binding.cnd_im_opts()
+    L.cnd_im_opts_init(ctypes.byref(o))
+    assert o.n_trials == 1024 and o.rng_seed == 1 and o.k == 0
+    out = np.zeros(4, dtype=np.int32)
+    # a NULL graph is rejected on the host, before any CUDA call
+    assert L.cnd_ic_im_celf(None, ctypes.byref(o), out.ctypes.data, None) == P.CND_EINVAL
+    assert "required" in P.cnd_last_error()
+
+
 def _graph():
     return I.erdos_renyi_m(50, 200, graph_seed=2)
 

@@ -1,0 +1,73 @@
+"""Lazy-greedy (CELF) influence maximisation on the GPU batch engine vs the oracle's CELF, exactly.
+
+The chosen seeds and every F(S_j) (sum of spreads over the common trials) must
+be identical: the lazy rule is fixed (include/cnd.h) and each F is an exact
+integer computed bit-exactly by the engine.
+"""
+import numpy as np
+import pytest
+
+from oracle import im
+import paper_2404_17059_gb300 as P
+from paper_2404_17059_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def er0():
+    g = I.erdos_renyi_m(1000, 10_000, graph_seed=1)
+    p = I.ic_uniform(g, 0.1)
+    w = I.lt_weighted_cascade(g)
+    return g, P.cnd_graph_create(g.n, g.row_ptr, g.col, p, w), p, w
+
+
+@pytest.mark.parametrize("batch", [1, 64])
+def test_ic_celf_er(er0, batch):
+    g, G, p, _ = er0
+    r = P.cnd_ic_im_celf(G, 5, 256, 1, eval_batch=batch)
+    s, f, ev = im.celf("ic", g, 5, 256, 1, eval_batch=batch, ic_prob=p)
+    np.testing.assert_array_equal(r.seeds, s)
+    np.testing.assert_array_equal(r.f, f)
+    assert r.evaluations <= ev and r.edge_checks > 0
+
+
+def test_lt_celf_er(er0):
+    g, G, _, w = er0
+    r = P.cnd_lt_im_celf(G, 4, 128, 5, eval_batch=8)
+    s, f, _ = im.celf("lt", g, 4, 128, 5, eval_batch=8, lt_weight=w)
+    np.testing.assert_array_equal(r.seeds, s)
+    np.testing.assert_array_equal(r.f, f)
+
+
+def test_celf_candidates_chunking_and_engine_options(er0):
+    g, G, p, _ = er0
+    cand = np.arange(3, g.n, 5, dtype=np.int32)[::-1].copy()
+    r = P.cnd_ic_im_celf(G, 4, 200, 2**40 + 3, candidates=cand, eval_batch=3, max_items=7, first_trial=1024,
+                         word_bits=128, chunk_edges=3)
+    s, f, _ = im.celf("ic", g, 4, 200, 2**40 + 3, candidates=cand, eval_batch=3, first_trial=1024, ic_prob=p)
+    np.testing.assert_array_equal(r.seeds, s)
+    np.testing.assert_array_equal(r.f, f)
+
+
+def test_celf_random_regular_wc():
+    """The paper's CELF benchmark graph shape: random 7-regular, n=5,000 (35,000 edges), WC IC."""
+    g = I.random_regular(5000, 7, graph_seed=1)
+    p = I.ic_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+    r = P.cnd_ic_im_celf(G, 6, 128, 1, graph=1)
+    s, f, _ = im.celf("ic", g, 6, 128, 1, ic_prob=p)
+    np.testing.assert_array_equal(r.seeds, s)
+    np.testing.assert_array_equal(r.f, f)
+
+
+def test_celf_rejects_bad_arguments(er0):
+    g, G, _, _ = er0
+    with pytest.raises(P.CndError):
+        P.cnd_ic_im_celf(G, 3, 64, 1, candidates=[1, 2])
+    with pytest.raises(P.CndError):
+        P.cnd_ic_im_celf(G, 1, 64, 1, candidates=[1, 1])
+    with pytest.raises(P.CndError):
+        P.cnd_ic_im_celf(G, 1, 0, 1)
+    with pytest.raises(P.CndError):
+        P.cnd_ic_im_celf(G, 1, 64, 1, candidates=[g.n])
