@@ -394,3 +394,33 @@ def batch_items(n: int, n_items: int, size_lo: int, size_hi: int, trial_choices,
     seeds = np.concatenate([uniform_seeds(n, int(s), rng) for s in sizes]) if n_items else np.zeros(0, np.int32)
     rng_seeds = np.arange(1, n_items + 1, dtype=np.uint64)
     return seed_off, seeds.astype(np.int32), trials.astype(np.int32), rng_seeds
+
+
+# ----------------------------------------------------------------------------- surrogate inputs
+SURROGATE_SHAPES = (  # parameter layout of the surrogate network: (name, rows, cols), fp32, row-major
+    ("Ws1", 64, 16), ("Wn1", 64, 16), ("b1", 64, 1), ("Ws2", 64, 64), ("Wn2", 64, 64), ("b2", 64, 1),
+    ("Ws3", 64, 64), ("Wn3", 64, 64), ("b3", 64, 1), ("wo", 64, 1), ("bo", 1, 1),
+)
+SURROGATE_N_PARAMS = sum(r * c for _, r, c in SURROGATE_SHAPES)
+
+
+def surrogate_init(graph_seed: int = 1) -> np.ndarray:
+    """Initial surrogate parameters: uniform on +-1/sqrt(fan_in) (fan-in of a layer counts both of
+    its inputs), drawn from numpy's Philox generator; fp32, flat, in SURROGATE_SHAPES order."""
+    rng = _rng(graph_seed + 0x5122)
+    fan_in = {"Ws1": 32, "Wn1": 32, "b1": 32, "Ws2": 128, "Wn2": 128, "b2": 128, "Ws3": 128, "Wn3": 128,
+              "b3": 128, "wo": 64, "bo": 64}
+    parts = [rng.uniform(-1.0, 1.0, size=r * c) / np.sqrt(fan_in[name]) for name, r, c in SURROGATE_SHAPES]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def surrogate_pairs(n: int, n_sets: int, size_lo: int = 1, size_hi: int = 50, graph_seed: int = 1):
+    """Training seed sets: sizes U{size_lo..size_hi}, distinct uniform nodes; returns (seed_off, seeds)."""
+    rng = _rng(graph_seed + 0x7A15)
+    sizes = rng.integers(size_lo, size_hi + 1, size=n_sets)
+    off = np.zeros(n_sets + 1, dtype=np.int64)
+    np.cumsum(sizes, out=off[1:])
+    seeds = np.empty(int(off[-1]), dtype=np.int32)
+    for i in range(n_sets):
+        seeds[off[i]:off[i + 1]] = rng.choice(n, size=int(sizes[i]), replace=False)
+    return off, seeds
