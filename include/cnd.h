@@ -292,6 +292,88 @@ cnd_status cnd_ic_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *see
 cnd_status cnd_lt_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *seeds_out, int64_t *f_out);
 
 /*
+ * Learned surrogate of IC activation frequencies, for screening candidate
+ * seeds in greedy influence maximisation (Sec. 2 "Influence Maximization";
+ * the paper has no learned component -- the exact simulator above stays the
+ * judge).  A 3-layer message-passing network, hidden width 64, maps a seed
+ * set S to yhat_v, a prediction of the fraction of trials in which node v
+ * ends active (the per-node counts of the paper's activation heatmap, Sec. 4,
+ * over the trial count):
+ *
+ *   q_e    = fp32(thr_e) * 2^-32, the live probability of edge e (thr_e the
+ *            IC threshold defined above; "always" gives 1)
+ *   x_v    = bf16([s_v, ln(1 + indeg v), ln(1 + outdeg v), 0 x 13])  (16 wide)
+ *   a^l_v  = bf16(sum over in-edges e = (u -> v) of q_e h^{l-1}_u)
+ *   h^l_v  = bf16(relu(W_s^l h^{l-1}_v + W_n^l a^l_v + b^l)),  h^0 = x, l = 1..3
+ *   yhat_v = s_v + (1 - s_v) sigmoid(w_o . h^3_v + b_o)
+ *   loss   = mean over v of (yhat_v - y_v)^2
+ *
+ * W_s, W_n are used as bf16 (tensor-core operands, fp32 accumulation); biases,
+ * w_o and b_o as fp32; the fp32 masters are what get_params returns.  The
+ * backward rounds dz = d loss / d z to bf16 before its products, like the
+ * forward's operands.  Parameters are one fp32 vector of CND_SUR_N_PARAMS
+ * values: [W_s^1 (64x16), W_n^1 (64x16), b^1 (64), W_s^2 (64x64), W_n^2,
+ * b^2, W_s^3, W_n^3, b^3, w_o (64), b_o (1)], matrices row-major (out x in).
+ *
+ * Host arrays throughout; a surrogate lives on its graph's device and owns
+ * its working memory (about 0.5 KB per node).  The graph needs IC
+ * probabilities.  Seed ids must lie in [0, n); duplicates count once.
+ */
+#define CND_SUR_N_PARAMS 18689
+typedef struct cnd_sur cnd_sur;
+
+/* params: host, CND_SUR_N_PARAMS fp32 values (required).  Adam state starts at zero. */
+cnd_status cnd_sur_create(const cnd_graph *g, const float *params, cnd_sur **out);
+void cnd_sur_destroy(cnd_sur *s); /* NULL-safe */
+cnd_status cnd_sur_set_params(cnd_sur *s, const float *params); /* also resets the Adam state */
+cnd_status cnd_sur_get_params(const cnd_sur *s, float *params_out);
+
+/* yhat_out: NULL or n floats; spread_out: NULL or sum of yhat (the predicted sigma(S)). */
+cnd_status cnd_sur_forward(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, float *yhat_out, double *spread_out);
+
+/* Loss for targets y (n floats) and its gradient (CND_SUR_N_PARAMS floats); either output may be NULL. */
+cnd_status cnd_sur_loss_grad(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, const float *y, double *loss_out,
+                             float *grad_out);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected; Kingma and Ba 2015) on the
+ * fp32 masters with the given gradient (host, CND_SUR_N_PARAMS floats). */
+cnd_status cnd_sur_adam(cnd_sur *s, const float *grad, float lr);
+
+/* Screening scores: score_out[c] (n floats) = the first-order gain of the predicted spread
+ * P = sum_v yhat_v when c joins S, (1 - s_c)(1 - sigmoid(o_c)) + d P / d x_c[0] through the
+ * network.  Seeds themselves get (1 - s_c) = 0 for the direct term. */
+cnd_status cnd_sur_scores(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, float *score_out);
+
+/*
+ * Training on pairs the simulator generates on the fly: pair i is a seed set
+ * of size U{set_size_lo..set_size_hi} of distinct uniform nodes (drawn from a
+ * splitmix64 stream of data_seed and i), with targets y_v = (trials in which
+ * v ends active) / n_trials from n_trials exact IC trials under key
+ * rng_seed + i (cnd_ic_simulate_batch).  Adam steps on the mean loss of
+ * batch_sets pairs; pairs first_pair .. first_pair + n_pairs - 1.
+ * loss_out: NULL or ceil(n_pairs / batch_sets) doubles, the mean loss of each
+ * step's batch (before the step).
+ */
+typedef struct {
+    int64_t first_pair;
+    int64_t n_pairs;
+    int32_t set_size_lo, set_size_hi;
+    int32_t n_trials;
+    int32_t batch_sets;   /* 0 = 16 */
+    int32_t sim_chunk;    /* pairs simulated per batched call, 0 = 256 */
+    float lr;             /* 0 = 1e-3 */
+    uint64_t data_seed;
+    uint64_t rng_seed;
+    void *stream;
+    double *sim_ms_out;   /* NULL or time spent in the simulator, ms */
+    double *train_ms_out; /* NULL or time spent in forward / backward / Adam, ms */
+    int64_t reserved[4];
+} cnd_sur_train_opts;
+
+void cnd_sur_train_opts_init(cnd_sur_train_opts *o);
+cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, double *loss_out);
+
+/*
  * Weighted-cascade LT weights for a CSR graph (Sec. 4 "Benchmarks", WC model:
  * the weight of every edge entering v is 1/in-degree(v)) in fixed point:
  * w_out[e] = floor((2^32 - 1) / in-degree(col[e])), so in-weights sum to at

@@ -26,7 +26,10 @@ EXPORTS = (
     "cnd_lt_simulate", "cnd_ic_simulate_ex", "cnd_lt_simulate_ex", "cnd_lt_weights_wc",
     "cnd_philox4x32_10", "cnd_last_error", "cnd_ic_simulate_noalloc", "cnd_ic_simulate_batch",
     "cnd_lt_simulate_batch", "cnd_autotune", "cnd_im_opts_init", "cnd_ic_im_celf", "cnd_lt_im_celf",
+    "cnd_sur_create", "cnd_sur_destroy", "cnd_sur_set_params", "cnd_sur_get_params", "cnd_sur_forward",
+    "cnd_sur_loss_grad", "cnd_sur_adam", "cnd_sur_scores", "cnd_sur_train_opts_init", "cnd_sur_train",
 )
+CND_SUR_N_PARAMS = 18689
 
 
 class CndError(RuntimeError):
@@ -100,6 +103,15 @@ class cnd_im_opts(C.Structure):
     ]
 
 
+class cnd_sur_train_opts(C.Structure):
+    _fields_ = [
+        ("first_pair", C.c_int64), ("n_pairs", C.c_int64), ("set_size_lo", C.c_int32), ("set_size_hi", C.c_int32),
+        ("n_trials", C.c_int32), ("batch_sets", C.c_int32), ("sim_chunk", C.c_int32), ("lr", C.c_float),
+        ("data_seed", C.c_uint64), ("rng_seed", C.c_uint64), ("stream", C.c_void_p), ("sim_ms_out", C.c_void_p),
+        ("train_ms_out", C.c_void_p), ("reserved", C.c_int64 * 4),
+    ]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -142,6 +154,25 @@ def load(build_if_missing: bool = True):
         for name in ("cnd_ic_im_celf", "cnd_lt_im_celf"):
             getattr(L, name).argtypes = [vp, C.POINTER(cnd_im_opts), vp, vp]
             getattr(L, name).restype = i32
+        L.cnd_sur_create.argtypes = [vp, vp, C.POINTER(vp)]
+        L.cnd_sur_create.restype = i32
+        L.cnd_sur_destroy.argtypes = [vp]
+        L.cnd_sur_destroy.restype = None
+        for name in ("cnd_sur_set_params", "cnd_sur_get_params"):
+            getattr(L, name).argtypes = [vp, vp]
+            getattr(L, name).restype = i32
+        L.cnd_sur_forward.argtypes = [vp, vp, i32, vp, vp]
+        L.cnd_sur_forward.restype = i32
+        L.cnd_sur_loss_grad.argtypes = [vp, vp, i32, vp, vp, vp]
+        L.cnd_sur_loss_grad.restype = i32
+        L.cnd_sur_adam.argtypes = [vp, vp, C.c_float]
+        L.cnd_sur_adam.restype = i32
+        L.cnd_sur_scores.argtypes = [vp, vp, i32, vp]
+        L.cnd_sur_scores.restype = i32
+        L.cnd_sur_train_opts_init.argtypes = [vp]
+        L.cnd_sur_train_opts_init.restype = None
+        L.cnd_sur_train.argtypes = [vp, C.POINTER(cnd_sur_train_opts), vp]
+        L.cnd_sur_train.restype = i32
         L.cnd_lt_weights_wc.argtypes = [i32, i32, vp, vp]
         L.cnd_lt_weights_wc.restype = i32
         L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
@@ -485,3 +516,106 @@ def cnd_ic_im_celf(g, k, n_trials, rng_seed, **kw) -> ImResult:
 
 def cnd_lt_im_celf(g, k, n_trials, rng_seed, **kw) -> ImResult:
     return _im_celf("cnd_lt_im_celf", g, k, n_trials, rng_seed, **kw)
+
+
+# ----------------------------------------------------------------------------- learned surrogate
+class CndSur:
+    """A surrogate network bound to a graph (cnd_sur); freed with cnd_sur_destroy or on collection."""
+
+    def __init__(self, handle, graph):
+        self.handle = handle
+        self.graph = graph  # keeps the graph alive
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            try:
+                load().cnd_sur_destroy(self.handle)
+            except Exception:
+                pass
+            self.handle = None
+
+
+def _seeds_arr(seeds):
+    a = np.ascontiguousarray(np.asarray(seeds, dtype=np.int32).ravel())
+    return a, (_np_ptr(a) if a.size else None)
+
+
+def cnd_sur_create(g: CndGraph, params) -> CndSur:
+    L = load()
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+    if p.size != CND_SUR_N_PARAMS:
+        raise ValueError(f"need {CND_SUR_N_PARAMS} parameters")
+    out = C.c_void_p()
+    _check(L.cnd_sur_create(g.handle, _np_ptr(p), C.byref(out)))
+    return CndSur(out, g)
+
+
+def cnd_sur_destroy(s: CndSur) -> None:
+    if s.handle:
+        load().cnd_sur_destroy(s.handle)
+        s.handle = None
+
+
+def cnd_sur_set_params(s: CndSur, params) -> None:
+    p = np.ascontiguousarray(np.asarray(params, dtype=np.float32).ravel())
+    if p.size != CND_SUR_N_PARAMS:
+        raise ValueError(f"need {CND_SUR_N_PARAMS} parameters")
+    _check(load().cnd_sur_set_params(s.handle, _np_ptr(p)))
+
+
+def cnd_sur_get_params(s: CndSur) -> np.ndarray:
+    p = np.empty(CND_SUR_N_PARAMS, dtype=np.float32)
+    _check(load().cnd_sur_get_params(s.handle, _np_ptr(p)))
+    return p
+
+
+def cnd_sur_forward(s: CndSur, seeds, *, yhat=True):
+    """(yhat float32 [n] or None, predicted spread sum(yhat))."""
+    sd, sp = _seeds_arr(seeds)
+    y = np.empty(s.graph.n, dtype=np.float32) if yhat else None
+    tot = C.c_double()
+    _check(load().cnd_sur_forward(s.handle, sp, int(sd.size), _np_ptr(y), C.byref(tot)))
+    return y, tot.value
+
+
+def cnd_sur_loss_grad(s: CndSur, seeds, y):
+    sd, sp = _seeds_arr(seeds)
+    yy = np.ascontiguousarray(np.asarray(y, dtype=np.float32).ravel())
+    if yy.size != s.graph.n:
+        raise ValueError("one target per node")
+    grad = np.empty(CND_SUR_N_PARAMS, dtype=np.float32)
+    loss = C.c_double()
+    _check(load().cnd_sur_loss_grad(s.handle, sp, int(sd.size), _np_ptr(yy), C.byref(loss), _np_ptr(grad)))
+    return loss.value, grad
+
+
+def cnd_sur_adam(s: CndSur, grad, lr: float) -> None:
+    gg = np.ascontiguousarray(np.asarray(grad, dtype=np.float32).ravel())
+    _check(load().cnd_sur_adam(s.handle, _np_ptr(gg), C.c_float(lr)))
+
+
+def cnd_sur_scores(s: CndSur, seeds) -> np.ndarray:
+    sd, sp = _seeds_arr(seeds)
+    out = np.empty(s.graph.n, dtype=np.float32)
+    _check(load().cnd_sur_scores(s.handle, sp, int(sd.size), _np_ptr(out)))
+    return out
+
+
+def cnd_sur_train(s: CndSur, n_pairs, *, first_pair=0, set_size=(1, 50), n_trials=1024, batch_sets=16,
+                  sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1, stream=None) -> dict:
+    L = load()
+    o = cnd_sur_train_opts()
+    L.cnd_sur_train_opts_init(C.byref(o))
+    o.first_pair, o.n_pairs = int(first_pair), int(n_pairs)
+    o.set_size_lo, o.set_size_hi = int(set_size[0]), int(set_size[1])
+    o.n_trials, o.batch_sets, o.sim_chunk, o.lr = int(n_trials), int(batch_sets), int(sim_chunk), float(lr)
+    o.data_seed, o.rng_seed, o.stream = int(data_seed), int(rng_seed), stream
+    sim_ms, train_ms = C.c_double(), C.c_double()
+    o.sim_ms_out = C.cast(C.pointer(sim_ms), C.c_void_p)
+    o.train_ms_out = C.cast(C.pointer(train_ms), C.c_void_p)
+    B = int(batch_sets) if batch_sets > 0 else 16
+    chunk = max(B, (int(sim_chunk) // B) * B) if sim_chunk > 0 else max(B, (256 // B) * B)
+    steps = sum(-(-min(chunk, n_pairs - c) // B) for c in range(0, int(n_pairs), chunk))
+    loss = np.zeros(max(steps, 1), dtype=np.float64)
+    _check(L.cnd_sur_train(s.handle, C.byref(o), _np_ptr(loss)))
+    return {"loss": loss[:steps], "sim_ms": sim_ms.value, "train_ms": train_ms.value}
