@@ -17,6 +17,13 @@ ingest happens once, before the timed region):
                     per edge; one batched IC call over the first K of 4,096 seed
                     sets (|S| ~ U{1..100}, trials from {256, 1024, 4096}).
   er1k              directed ER n=1,000, m=10,000, p=0.1, 10 seeds, 1,000 trials.
+  surrogate         the learned screen: R-MAT scale 17 (2^21 samples deduplicated),
+                    weighted-cascade IC; the network is trained on --pairs seed
+                    sets (|S| ~ U{1..50}, 1,024 exact trials each, generated on
+                    the fly by the simulator), then greedy k=50 with the
+                    surrogate as a screen is timed against MC CELF (1,024
+                    common trials); both seed sets are judged with 10,000
+                    exact trials.  metric: CELF time / screened-greedy time.
   celf_rr7          influence maximisation: CELF with k=10 on a random 7-regular
                     graph, n=5,000 (35,000 directed edges), IC with trivalency and
                     weighted-cascade probabilities, 1,000 common trials per
@@ -392,6 +399,91 @@ def run_celf(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- surrogate
+def run_surrogate(args):
+    import torch
+    import paper_2404_17059_gb300 as P
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    k, T, judge_T, judge_key = args.k, 1024, 10_000, 7777
+    g = I.rmat(17, 1 << 21, graph_seed=1)
+    p = I.ic_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+    # held-out sets and their exact per-node frequencies
+    ho_off, ho_seeds = I.surrogate_pairs(g.n, 64, 1, 50, graph_seed=99)
+    ho_keys = np.arange(1_000_000, 1_000_064, dtype=np.uint64)
+    ho = P.cnd_ic_simulate_batch(G, ho_off, ho_seeds, np.full(64, T, dtype=np.int32), ho_keys, node_count=True)
+    freq = ho.node_count.reshape(64, g.n).astype(np.float64) / T
+
+    def quality(sur):
+        err, mse = [], []
+        for i in range(64):
+            yh, tot = P.cnd_sur_forward(sur, ho_seeds[ho_off[i]:ho_off[i + 1]])
+            mc = freq[i].sum()
+            err.append(abs(tot - mc) / mc)
+            mse.append(float(np.mean((yh - freq[i]) ** 2)))
+        return {"spread_rel_err_mean": float(np.mean(err)), "spread_rel_err_max": float(np.max(err)),
+                "node_mse": float(np.mean(mse))}
+
+    init = I.surrogate_init(1)
+    sur = P.cnd_sur_create(G, init)
+    untrained = P.cnd_sur_create(G, init)
+    q0 = quality(sur)
+    t0 = time.perf_counter()
+    tr = P.cnd_sur_train(sur, args.pairs, n_trials=T, batch_sets=16, sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1)
+    train_s = time.perf_counter() - t0
+    q1 = quality(sur)
+
+    def judge(seeds):
+        r = P.cnd_ic_simulate_ex(G, seeds, judge_T, judge_key, node_count=False)
+        return float(r.spread.astype(np.float64).mean())
+
+    runs = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc = P.cnd_ic_im_celf(G, k, T, 1, graph=1)
+    runs["mc_celf"] = {"s": time.perf_counter() - t0, "seeds": rc.seeds.tolist(), "evaluations": rc.evaluations,
+                       "edge_checks": rc.edge_checks}
+    variants = (("screened_trained", sur, args.screen_mode), ("screened_trained_gradient", sur, "gradient"),
+                ("screened_trained_onehop", sur, "onehop"), ("screened_untrained", untrained, args.screen_mode),
+                ("screened_degree_no_network", None, "degree"))
+    for name, model, mode in variants:
+        if name != "screened_trained" and mode == args.screen_mode and model is sur:
+            continue
+        t0 = time.perf_counter()
+        rs, tm = P.cnd_ic_im_screened(G, model, k, T, 1, n_screen=args.screen, n_exact=args.exact, mode=mode,
+                                      graph=1)
+        runs[name] = {"s": time.perf_counter() - t0, "mode": mode, "seeds": rs.seeds.tolist(),
+                      "evaluations": rs.evaluations, "edge_checks": rs.edge_checks, **tm}
+    for v in runs.values():
+        v["judged_spread"] = judge(v["seeds"])
+    base = runs["mc_celf"]
+    for name in runs:
+        if name == "mc_celf":
+            continue
+        runs[name]["spread_vs_celf"] = runs[name]["judged_spread"] / base["judged_spread"]
+        runs[name]["speedup_vs_celf"] = base["s"] / runs[name]["s"]
+    line = {"metric": "surrogate vs MC greedy speedup", "value": runs["screened_trained"]["speedup_vs_celf"],
+            "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * runs["screened_trained"]["s"],
+            "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None, "dtype": "bf16+u64",
+            "data": "synthetic",
+            "config": {"workload": f"R-MAT scale 17 ({g.m} directed edges), WC IC; surrogate trained on "
+                                   f"{args.pairs} pairs (|S|~U{{1..50}}, {T} trials); greedy k={k} screened "
+                                   f"({args.screen} by the {args.screen_mode} score, then by predicted spread, "
+                                   f"{args.exact} simulated per round) vs MC CELF, "
+                                   f"{T} common trials; judged with {judge_T} trials (key {judge_key})",
+                       "name": "surrogate"},
+            "spread_vs_celf": runs["screened_trained"]["spread_vs_celf"],
+            "training": {"pairs": args.pairs, "s": train_s, "sim_ms": tr["sim_ms"], "train_ms": tr["train_ms"],
+                         "loss_first": float(tr["loss"][:8].mean()), "loss_last": float(tr["loss"][-8:].mean())},
+            "speedup_including_training": base["s"] / (runs["screened_trained"]["s"] + train_s),
+            "heldout_untrained": q0, "heldout_trained": q1, "runs": runs}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- our arm
 KERNEL = {"ic": "k_push<0>", "lt": "k_push<1>"}
 
@@ -558,7 +650,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ba100k",
-                    choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7"])
+                    choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7", "surrogate"])
+    ap.add_argument("--pairs", type=int, default=200_000, help="surrogate: training pairs")
+    ap.add_argument("--k", type=int, default=50, help="surrogate: seeds to choose")
+    ap.add_argument("--screen", type=int, default=64, help="surrogate: candidates kept by the gradient score")
+    ap.add_argument("--exact", type=int, default=8, help="surrogate: candidates simulated per round")
+    ap.add_argument("--screen-mode", default="onehop", choices=["gradient", "onehop"],
+                    help="surrogate: first score of the screen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trials", type=int, default=0, help="override the workload's trials per model")
     ap.add_argument("--items", type=int, default=0, help="rmat20batch: seed sets per step (default 64)")
@@ -573,6 +671,8 @@ def main():
         return run_reference(args)
     if args.workload == "celf_rr7":
         return run_celf(args)
+    if args.workload == "surrogate":
+        return run_surrogate(args)
     return run_ours(args)
 
 

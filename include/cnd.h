@@ -344,6 +344,10 @@ cnd_status cnd_sur_adam(cnd_sur *s, const float *grad, float lr);
  * network.  Seeds themselves get (1 - s_c) = 0 for the direct term. */
 cnd_status cnd_sur_scores(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, float *score_out);
 
+/* One-hop expected gain under the prediction yhat = yhat(S): score_out[c] (n floats) =
+ * (1 - yhat_c) (1 + sum over out-edges (c -> w) of q_e (1 - yhat_w)). */
+cnd_status cnd_sur_onehop(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, float *score_out);
+
 /*
  * Training on pairs the simulator generates on the fly: pair i is a seed set
  * of size U{set_size_lo..set_size_hi} of distinct uniform nodes (drawn from a
@@ -372,6 +376,39 @@ typedef struct {
 
 void cnd_sur_train_opts_init(cnd_sur_train_opts *o);
 cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, double *loss_out);
+
+/*
+ * Greedy influence maximisation with the surrogate as a screen (IC).  Each of
+ * the k rounds, with S the seeds chosen so far:
+ *   1. score every candidate c not in S and keep the n_screen best (ties:
+ *      lower id).  mode 0: cnd_sur_scores (one forward and one backward
+ *      pass); mode 1: the expected one-hop gain under the network's
+ *      prediction yhat = yhat(S) (one forward pass),
+ *        (1 - yhat_c) (1 + sum over out-edges (c -> w) of q_e (1 - yhat_w));
+ *      mode 2: out-degree (no network: the screen without the surrogate);
+ *   2. if n_screen > n_exact, re-rank those by the surrogate's predicted
+ *      spread of S + c (one forward each) and keep the n_exact best;
+ *   3. evaluate F(S + c) exactly for the survivors with the batched Monte
+ *      Carlo engine (common random numbers as in CELF: trials first_trial ..
+ *      first_trial + n_trials - 1 of key rng_seed) and choose the best
+ *      (ties: lower id).
+ * The simulator is the judge of every choice; the network only decides which
+ * candidates it sees.  o->k, n_trials, rng_seed, candidates, max_items, sim,
+ * stream, evaluations_out and edge_checks_out as for CELF (eval_batch
+ * unused).  seeds_out[j], f_out[j] (may be NULL) as for CELF.
+ */
+typedef struct {
+    int32_t n_screen;     /* candidates kept by the first score, >= n_exact (0 = n_exact) */
+    int32_t n_exact;      /* candidates simulated per round, >= 1 */
+    int32_t mode;         /* first score: 0 gradient, 1 one-hop gain, 2 out-degree */
+    int32_t pad;
+    double *sur_ms_out;   /* NULL or wall time in the surrogate, ms */
+    double *sim_ms_out;   /* NULL or wall time in the simulator, ms */
+    int64_t reserved[3];
+} cnd_screen_opts;
+
+cnd_status cnd_ic_im_screened(const cnd_graph *g, cnd_sur *s, const cnd_im_opts *o, const cnd_screen_opts *so,
+                              int32_t *seeds_out, int64_t *f_out);
 
 /*
  * Weighted-cascade LT weights for a CSR graph (Sec. 4 "Benchmarks", WC model:

@@ -36,6 +36,9 @@ predicted spread P = sum_v yhat_v when c joins S): the same backward with
 g_v = (1 - s_v) sig'(o_v), carried down to the seed-indicator input:
   score_c = (1 - s_c)(1 - sig(o_c)) + [W_s^{1T} e^1_c]_0 + sum over out-edges (c -> w) of q [W_n^{1T} e^1_w]_0
 
+One-hop screening score (needs only the forward): with yhat = yhat(S),
+  onehop_c = (1 - yhat_c) (1 + sum over out-edges (c -> w) of q (1 - yhat_w))
+
 Parameters travel as one fp32 vector in the order
   [W_s^1 (64x16), W_n^1 (64x16), b^1, W_s^2 (64x64), W_n^2, b^2, W_s^3, W_n^3, b^3, w_o (64), b_o]
 (matrices row-major, out x in): 18,689 values.
@@ -183,6 +186,13 @@ def screen_scores(flat, G: Graph, seeds):
     g = (1.0 - s) * sig * (1.0 - sig)
     _, dx0 = backward(c, G, g, want_input_grad=True)
     return (1.0 - s) * (1.0 - sig) + dx0[:, 0], c
+
+
+def onehop_scores(flat, G: Graph, seeds):
+    """Expected one-hop gain under yhat = yhat(S): (1 - yhat_c)(1 + sum over out-edges (c -> w) of q (1 - yhat_w))."""
+    c = forward(flat, G, seeds)
+    y = c["yhat"]
+    return (1.0 - y) * (1.0 + G.A_out @ (1.0 - y)), c
 
 
 def adam(flat, grad, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):

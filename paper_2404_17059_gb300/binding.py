@@ -28,6 +28,7 @@ EXPORTS = (
     "cnd_lt_simulate_batch", "cnd_autotune", "cnd_im_opts_init", "cnd_ic_im_celf", "cnd_lt_im_celf",
     "cnd_sur_create", "cnd_sur_destroy", "cnd_sur_set_params", "cnd_sur_get_params", "cnd_sur_forward",
     "cnd_sur_loss_grad", "cnd_sur_adam", "cnd_sur_scores", "cnd_sur_train_opts_init", "cnd_sur_train",
+    "cnd_ic_im_screened", "cnd_sur_onehop",
 )
 CND_SUR_N_PARAMS = 18689
 
@@ -112,6 +113,11 @@ class cnd_sur_train_opts(C.Structure):
     ]
 
 
+class cnd_screen_opts(C.Structure):
+    _fields_ = [("n_screen", C.c_int32), ("n_exact", C.c_int32), ("mode", C.c_int32), ("pad", C.c_int32),
+                ("sur_ms_out", C.c_void_p), ("sim_ms_out", C.c_void_p), ("reserved", C.c_int64 * 3)]
+
+
 def library_path() -> str:
     return _build.LIB
 
@@ -167,12 +173,15 @@ def load(build_if_missing: bool = True):
         L.cnd_sur_loss_grad.restype = i32
         L.cnd_sur_adam.argtypes = [vp, vp, C.c_float]
         L.cnd_sur_adam.restype = i32
-        L.cnd_sur_scores.argtypes = [vp, vp, i32, vp]
-        L.cnd_sur_scores.restype = i32
+        for name in ("cnd_sur_scores", "cnd_sur_onehop"):
+            getattr(L, name).argtypes = [vp, vp, i32, vp]
+            getattr(L, name).restype = i32
         L.cnd_sur_train_opts_init.argtypes = [vp]
         L.cnd_sur_train_opts_init.restype = None
         L.cnd_sur_train.argtypes = [vp, C.POINTER(cnd_sur_train_opts), vp]
         L.cnd_sur_train.restype = i32
+        L.cnd_ic_im_screened.argtypes = [vp, vp, C.POINTER(cnd_im_opts), C.POINTER(cnd_screen_opts), vp, vp]
+        L.cnd_ic_im_screened.restype = i32
         L.cnd_lt_weights_wc.argtypes = [i32, i32, vp, vp]
         L.cnd_lt_weights_wc.restype = i32
         L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
@@ -477,8 +486,7 @@ class ImResult:
     edge_checks: int
 
 
-def _im_celf(fn_name, g, k, n_trials, rng_seed, *, candidates=None, eval_batch=0, max_items=0, first_trial=0,
-             stream=None, **sim_kw) -> ImResult:
+def _im_opts(k, n_trials, rng_seed, candidates, eval_batch, max_items, first_trial, stream, sim_kw):
     L = load()
     o = cnd_im_opts()
     L.cnd_im_opts_init(C.byref(o))
@@ -502,10 +510,16 @@ def _im_celf(fn_name, g, k, n_trials, rng_seed, *, candidates=None, eval_batch=0
     ec = C.c_int64()
     o.evaluations_out = C.cast(C.pointer(ev), C.c_void_p)
     o.edge_checks_out = C.cast(C.pointer(ec), C.c_void_p)
+    return o, (cand, so, ev, ec)
+
+
+def _im_celf(fn_name, g, k, n_trials, rng_seed, *, candidates=None, eval_batch=0, max_items=0, first_trial=0,
+             stream=None, **sim_kw) -> ImResult:
+    o, keep = _im_opts(k, n_trials, rng_seed, candidates, eval_batch, max_items, first_trial, stream, sim_kw)
     seeds = np.empty(int(k), dtype=np.int32)
     f = np.empty(int(k), dtype=np.int64)
-    _check(getattr(L, fn_name)(g.handle, C.byref(o), _np_ptr(seeds), _np_ptr(f)))
-    return ImResult(seeds, f, ev.value, ec.value)
+    _check(getattr(load(), fn_name)(g.handle, C.byref(o), _np_ptr(seeds), _np_ptr(f)))
+    return ImResult(seeds, f, keep[2].value, keep[3].value)
 
 
 def cnd_ic_im_celf(g, k, n_trials, rng_seed, **kw) -> ImResult:
@@ -601,6 +615,13 @@ def cnd_sur_scores(s: CndSur, seeds) -> np.ndarray:
     return out
 
 
+def cnd_sur_onehop(s: CndSur, seeds) -> np.ndarray:
+    sd, sp = _seeds_arr(seeds)
+    out = np.empty(s.graph.n, dtype=np.float32)
+    _check(load().cnd_sur_onehop(s.handle, sp, int(sd.size), _np_ptr(out)))
+    return out
+
+
 def cnd_sur_train(s: CndSur, n_pairs, *, first_pair=0, set_size=(1, 50), n_trials=1024, batch_sets=16,
                   sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1, stream=None) -> dict:
     L = load()
@@ -619,3 +640,23 @@ def cnd_sur_train(s: CndSur, n_pairs, *, first_pair=0, set_size=(1, 50), n_trial
     loss = np.zeros(max(steps, 1), dtype=np.float64)
     _check(L.cnd_sur_train(s.handle, C.byref(o), _np_ptr(loss)))
     return {"loss": loss[:steps], "sim_ms": sim_ms.value, "train_ms": train_ms.value}
+
+
+SCREEN_MODES = {"gradient": 0, "onehop": 1, "degree": 2}
+
+
+def cnd_ic_im_screened(g, sur, k, n_trials, rng_seed, *, n_screen=64, n_exact=4, mode="gradient", candidates=None,
+                       max_items=0, first_trial=0, stream=None, **sim_kw):
+    """Greedy IC influence maximisation with the surrogate as a screen; returns (ImResult, timings)."""
+    o, keep = _im_opts(k, n_trials, rng_seed, candidates, 0, max_items, first_trial, stream, sim_kw)
+    so = cnd_screen_opts()
+    so.n_screen, so.n_exact = int(n_screen), int(n_exact)
+    so.mode = SCREEN_MODES[mode] if isinstance(mode, str) else int(mode)
+    sur_ms, sim_ms = C.c_double(), C.c_double()
+    so.sur_ms_out = C.cast(C.pointer(sur_ms), C.c_void_p)
+    so.sim_ms_out = C.cast(C.pointer(sim_ms), C.c_void_p)
+    seeds = np.empty(int(k), dtype=np.int32)
+    f = np.empty(int(k), dtype=np.int64)
+    _check(load().cnd_ic_im_screened(g.handle, sur.handle if sur is not None else None, C.byref(o), C.byref(so),
+                                     _np_ptr(seeds), _np_ptr(f)))
+    return ImResult(seeds, f, keep[2].value, keep[3].value), {"sur_ms": sur_ms.value, "sim_ms": sim_ms.value}

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
+#include <numeric>
 #include <queue>
 #include <vector>
 
@@ -148,6 +150,8 @@ class Evaluator {
     int64_t evals_ = 0, checks_ = 0;
 };
 
+cnd_status candidates_of(const cnd_graph_dev &G, const cnd_im_opts *o, const char *fn, std::vector<int32_t> &cand);
+
 cnd_status celf(int model, const cnd_graph *g, const cnd_im_opts *o, int32_t *seeds_out, int64_t *f_out) {
     const char *fn = model == 0 ? "cnd_ic_im_celf" : "cnd_lt_im_celf";
     clear_error();
@@ -165,23 +169,9 @@ cnd_status celf(int model, const cnd_graph *g, const cnd_im_opts *o, int32_t *se
         return CND_EINVAL;
     }
     std::vector<int32_t> cand;
-    std::vector<char> seen((size_t)G.n, 0);
-    if (o->candidates) {
-        if (o->n_candidates < 0) {
-            set_error("%s: n_candidates < 0", fn);
-            return CND_EINVAL;
-        }
-        cand.assign(o->candidates, o->candidates + o->n_candidates);
-        for (int32_t v : cand) {
-            if (v < 0 || v >= G.n || seen[(size_t)v]) {
-                set_error("%s: candidate %d out of range or repeated", fn, (int)v);
-                return CND_EINVAL;
-            }
-            seen[(size_t)v] = 1;
-        }
-    } else {
-        cand.resize((size_t)G.n);
-        for (int32_t v = 0; v < G.n; ++v) cand[(size_t)v] = v;
+    {
+        const cnd_status cs = candidates_of(G, o, fn, cand);
+        if (cs != CND_OK) return cs;
     }
     if (o->k < 1 || (size_t)o->k > cand.size()) {
         set_error("%s: k = %d must be in 1 .. number of candidates (%zu)", fn, (int)o->k, cand.size());
@@ -244,10 +234,151 @@ cnd_status celf(int model, const cnd_graph *g, const cnd_im_opts *o, int32_t *se
     return CND_OK;
 }
 
+cnd_status candidates_of(const cnd_graph_dev &G, const cnd_im_opts *o, const char *fn, std::vector<int32_t> &cand) {
+    std::vector<char> seen((size_t)G.n, 0);
+    if (o->candidates) {
+        if (o->n_candidates < 0) {
+            set_error("%s: n_candidates < 0", fn);
+            return CND_EINVAL;
+        }
+        cand.assign(o->candidates, o->candidates + o->n_candidates);
+        for (int32_t v : cand) {
+            if (v < 0 || v >= G.n || seen[(size_t)v]) {
+                set_error("%s: candidate %d out of range or repeated", fn, (int)v);
+                return CND_EINVAL;
+            }
+            seen[(size_t)v] = 1;
+        }
+    } else {
+        cand.resize((size_t)G.n);
+        std::iota(cand.begin(), cand.end(), 0);
+    }
+    return CND_OK;
+}
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0) { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
+
+// indices of the best `keep` entries by (value descending, node ascending)
+std::vector<int32_t> top_by(const std::vector<int32_t> &nodes, const std::vector<double> &val, size_t keep) {
+    std::vector<size_t> idx(nodes.size());
+    std::iota(idx.begin(), idx.end(), 0);
+    keep = std::min(keep, idx.size());
+    auto better = [&](size_t a, size_t b) { return val[a] != val[b] ? val[a] > val[b] : nodes[a] < nodes[b]; };
+    std::partial_sort(idx.begin(), idx.begin() + keep, idx.end(), better);
+    std::vector<int32_t> out(keep);
+    for (size_t i = 0; i < keep; ++i) out[i] = nodes[idx[i]];
+    return out;
+}
+
+cnd_status screened(const cnd_graph *g, cnd_sur *sur, const cnd_im_opts *o, const cnd_screen_opts *so,
+                    int32_t *seeds_out, int64_t *f_out) {
+    const char *fn = "cnd_ic_im_screened";
+    clear_error();
+    if (!g || !o || !so || !seeds_out || (!sur && so->mode != 2)) {
+        set_error("%s: graph, surrogate (modes 0, 1), options and seeds_out are required", fn);
+        return CND_EINVAL;
+    }
+    const cnd_graph_dev &G = g->d;
+    if (!G.ic_edge && G.m > 0) {
+        set_error("%s: graph was created without IC probabilities", fn);
+        return CND_EINVAL;
+    }
+    if (o->n_trials < 1 || o->n_trials > INT32_MAX || so->n_exact < 1 ||
+        (so->n_screen != 0 && so->n_screen < so->n_exact) || so->mode < 0 || so->mode > 2) {
+        set_error("%s: need 1 <= n_trials <= 2^31-1, n_exact >= 1, n_screen 0 or >= n_exact, mode 0..2", fn);
+        return CND_EINVAL;
+    }
+    std::vector<int32_t> cand;
+    cnd_status s = candidates_of(G, o, fn, cand);
+    if (s != CND_OK) return s;
+    if (o->k < 1 || (size_t)o->k > cand.size()) {
+        set_error("%s: k = %d must be in 1 .. number of candidates (%zu)", fn, (int)o->k, cand.size());
+        return CND_EINVAL;
+    }
+    int dev = 0;
+    DeviceGuard guard;
+    CND_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != G.device) {
+        CND_CUDA_TRY(cudaSetDevice(G.device));
+        guard.prev = dev;
+    }
+    Evaluator ev(0, g, *o, static_cast<cudaStream_t>(o->stream));
+    s = ev.init(o->k);
+    if (s != CND_OK) return s;
+    const size_t n_screen = (size_t)(so->n_screen > 0 ? so->n_screen : so->n_exact);
+    const size_t n_exact = (size_t)so->n_exact;
+    std::vector<char> is_cand((size_t)G.n, 0);
+    for (int32_t v : cand) is_cand[(size_t)v] = 1;
+    std::vector<int32_t> S, pool, one;
+    std::vector<float> score((size_t)G.n);
+    if (so->mode == 2) {
+        std::vector<int32_t> rp((size_t)G.n + 1);
+        CND_CUDA_TRY(cudaMemcpy(rp.data(), G.row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost));
+        for (int32_t v = 0; v < G.n; ++v) score[(size_t)v] = (float)(rp[(size_t)v + 1] - rp[(size_t)v]);
+    }
+    std::vector<double> val;
+    std::vector<int64_t> F;
+    double sur_ms = 0.0, sim_ms = 0.0;
+    int64_t fS = 0;
+    for (int32_t j = 0; j < o->k; ++j) {
+        auto t0 = Clock::now();
+        if (so->mode == 0)
+            s = cnd_sur_scores(sur, S.data(), (int32_t)S.size(), score.data());
+        else if (so->mode == 1)
+            s = cnd_sur_onehop(sur, S.data(), (int32_t)S.size(), score.data());
+        if (s != CND_OK) return s;
+        pool.clear();
+        val.clear();
+        for (int32_t v : cand)
+            if (is_cand[(size_t)v]) {
+                pool.push_back(v);
+                val.push_back((double)score[(size_t)v]);
+            }
+        std::vector<int32_t> keep = top_by(pool, val, n_screen);
+        if (keep.size() > n_exact) {
+            val.assign(keep.size(), 0.0);
+            for (size_t i = 0; i < keep.size(); ++i) {
+                one = S;
+                one.push_back(keep[i]);
+                double pred = 0.0;
+                s = cnd_sur_forward(sur, one.data(), (int32_t)one.size(), nullptr, &pred);
+                if (s != CND_OK) return s;
+                val[i] = pred;
+            }
+            keep = top_by(keep, val, n_exact);
+        }
+        sur_ms += ms_since(t0);
+        t0 = Clock::now();
+        s = ev.eval(S, keep, F);
+        if (s != CND_OK) return s;
+        sim_ms += ms_since(t0);
+        size_t best = 0;
+        for (size_t i = 1; i < keep.size(); ++i)
+            if (F[i] > F[best] || (F[i] == F[best] && keep[i] < keep[best])) best = i;
+        S.push_back(keep[best]);
+        is_cand[(size_t)keep[best]] = 0;
+        fS = F[best];
+        seeds_out[j] = keep[best];
+        if (f_out) f_out[j] = fS;
+    }
+    if (o->evaluations_out) *o->evaluations_out = ev.evaluations();
+    if (o->edge_checks_out) *o->edge_checks_out = ev.edge_checks();
+    if (so->sur_ms_out) *so->sur_ms_out = sur_ms;
+    if (so->sim_ms_out) *so->sim_ms_out = sim_ms;
+    return CND_OK;
+}
+
 }  // namespace
 }  // namespace cnd
 
 extern "C" {
+
+cnd_status cnd_ic_im_screened(const cnd_graph *g, cnd_sur *s, const cnd_im_opts *o, const cnd_screen_opts *so,
+                              int32_t *seeds_out, int64_t *f_out) {
+    return cnd::screened(g, s, o, so, seeds_out, f_out);
+}
 
 void cnd_im_opts_init(cnd_im_opts *o) {
     if (!o) return;

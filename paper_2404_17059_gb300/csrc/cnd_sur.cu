@@ -652,6 +652,19 @@ __global__ void k_scores(int32_t n, const float *__restrict__ o, const __nv_bflo
     }
 }
 
+// (1 - yhat_c) (1 + sum over out-edges of q (1 - yhat_w)); a thread per node
+__global__ void k_onehop(int32_t n, const int32_t *__restrict__ row_ptr, const uint2 *__restrict__ ic_edge,
+                         const float *__restrict__ yhat, float *__restrict__ score) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < n; c += gridDim.x * blockDim.x) {
+        float s = 1.0f;
+        for (int32_t e = row_ptr[c]; e < row_ptr[c + 1]; ++e) {
+            const uint2 ed = ic_edge[e];
+            s += edge_q(ed.y) * (1.0f - yhat[ed.x]);
+        }
+        score[c] = (1.0f - yhat[c]) * s;
+    }
+}
+
 __global__ void k_adam(int32_t np, float *__restrict__ p, const float *__restrict__ grad, float gscale,
                        float *__restrict__ m, float *__restrict__ v, float lr, float c1, float c2) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
@@ -1113,6 +1126,33 @@ cnd_status cnd_sur_scores(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, flo
     seed_clear(s, s->seeds, ns, cs);
     CND_CUDA_TRY(cudaGetLastError());
     CND_CUDA_TRY(cudaMemcpyAsync(score_out, s->yv, sizeof(float) * n, cudaMemcpyDeviceToHost, cs));
+    CND_CUDA_TRY(cudaStreamSynchronize(cs));
+    return CND_OK;
+}
+
+cnd_status cnd_sur_onehop(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, float *score_out) {
+    clear_error();
+    cnd_status st = check_sur(s, "cnd_sur_onehop");
+    if (st != CND_OK) return st;
+    if (!score_out) {
+        set_error("cnd_sur_onehop: score_out is NULL");
+        return CND_EINVAL;
+    }
+    DevGuard gd;
+    if ((st = enter(s, gd)) != CND_OK) return st;
+    cudaStream_t cs = nullptr;
+    int32_t ns = 0;
+    if ((st = upload_seeds(s, seeds, n_seeds, ns, cs, "cnd_sur_onehop")) != CND_OK) return st;
+    const int32_t n = s->n;
+    seed_set(s, s->seeds, ns, cs);
+    forward(s, cs);
+    CND_CUDA_TRY(cudaMemsetAsync(s->dsum, 0, sizeof(double), cs));
+    k_yhat<<<grid_for(n, 256, s->num_sms), 256, 0, cs>>>(n, s->o, s->x, s->yv, s->dsum);
+    const cnd_graph_dev &G = s->g->d;
+    k_onehop<<<grid_for(n, 256, s->num_sms), 256, 0, cs>>>(n, G.row_ptr, G.ic_edge, s->yv, s->ds0);
+    seed_clear(s, s->seeds, ns, cs);
+    CND_CUDA_TRY(cudaGetLastError());
+    CND_CUDA_TRY(cudaMemcpyAsync(score_out, s->ds0, sizeof(float) * n, cudaMemcpyDeviceToHost, cs));
     CND_CUDA_TRY(cudaStreamSynchronize(cs));
     return CND_OK;
 }

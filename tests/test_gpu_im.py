@@ -7,6 +7,7 @@ integer computed bit-exactly by the engine.
 import numpy as np
 import pytest
 
+import oracle
 from oracle import im
 import paper_2404_17059_gb300 as P
 from paper_2404_17059_gb300 import inputs as I
@@ -71,3 +72,25 @@ def test_celf_rejects_bad_arguments(er0):
         P.cnd_ic_im_celf(G, 1, 0, 1)
     with pytest.raises(P.CndError):
         P.cnd_ic_im_celf(G, 1, 64, 1, candidates=[g.n])
+
+
+def test_screened_greedy_without_screening_is_plain_greedy(er0):
+    """With every candidate passed to the simulator the surrogate decides nothing: plain greedy."""
+    g, G, p, _ = er0
+    cand = np.arange(0, g.n, 4, dtype=np.int32)
+    sur = P.cnd_sur_create(G, I.surrogate_init(2))
+    r, tm = P.cnd_ic_im_screened(G, sur, 3, 256, 7, n_screen=cand.size, n_exact=cand.size, candidates=cand)
+    s, f = im.greedy("ic", g, 3, 256, 7, candidates=cand, ic_prob=p)
+    np.testing.assert_array_equal(r.seeds, s)
+    np.testing.assert_array_equal(r.f, f)
+    assert tm["sim_ms"] > 0 and tm["sur_ms"] > 0
+
+
+def test_screened_greedy_values_are_exact(er0):
+    g, G, p, _ = er0
+    sur = P.cnd_sur_create(G, I.surrogate_init(3))
+    r, _ = P.cnd_ic_im_screened(G, sur, 5, 128, 3, n_screen=32, n_exact=3)
+    assert len(set(r.seeds.tolist())) == 5 and r.evaluations == 5 * 3
+    for j in range(5):
+        ref = oracle.simulate("ic", g, r.seeds[:j + 1], 128, 3, ic_prob=p, level_counts_len=0)
+        assert r.f[j] == int(ref.spread.astype(np.int64).sum())

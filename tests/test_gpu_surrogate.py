@@ -133,3 +133,11 @@ def test_training_reduces_loss():
     loss = r["loss"]
     assert loss.size == 128 and np.all(np.isfinite(loss))
     assert loss[-16:].mean() < 0.5 * loss[:4].mean()
+
+
+def test_onehop_scores_match_oracle(setup):
+    g, OG, G, sur, params = setup
+    seeds = _seeds(g, 9, 41)
+    sc = P.cnd_sur_onehop(sur, seeds)
+    ref, _ = S.onehop_scores(params.astype(np.float64), OG, seeds)
+    np.testing.assert_allclose(sc, ref, rtol=1e-2, atol=1e-2)

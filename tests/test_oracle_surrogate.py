@@ -136,3 +136,16 @@ def test_adam_first_step_is_signed_lr():
     np.testing.assert_allclose(w1, w - 0.01 * g / (np.abs(g) + 1e-8), rtol=0, atol=1e-15)
     np.testing.assert_allclose(m, 0.1 * g)
     np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_onehop_score_closed_form():
+    """Out-star centre 0 -> leaves 1..5 with q = 1/2: with a network predicting 0 everywhere off the seeds,
+    the centre's score is 1 + 5/2 and a leaf's is 1; with the centre seeded, leaves still score 1, centre 0."""
+    g = I.out_star(5)
+    G = S.Graph(g, I.ic_uniform(g, 0.5))
+    flat = np.zeros(S.N_PARAMS)
+    flat[-1] = -80.0  # sigmoid(o) = e^-80: zero to double precision next to 1
+    sc, _ = S.onehop_scores(flat, G, [])
+    np.testing.assert_allclose(sc, [3.5, 1, 1, 1, 1, 1], rtol=1e-12)
+    sc, _ = S.onehop_scores(flat, G, [0])
+    np.testing.assert_allclose(sc, [0, 1, 1, 1, 1, 1], rtol=1e-12)
