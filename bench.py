@@ -67,6 +67,9 @@ from paper_2404_17059_gb300 import inputs as I  # noqa: E402
 METRIC = "IC/LT edge checks/sec and trials/sec at 1 GB300 (% of HBM peak); surrogate vs MC greedy speedup"
 UNIT = "edge_checks/s"
 FALLBACK_HBM_GBS = 6800.0
+# Philox-4x32-10 = 10 rounds x two 32x32->64-bit products = 40 32-bit multiply results per call;
+# 152 SMs x 64 integer multiplies per clock x 2.07 GHz (maximum SM clock)
+PHILOX_PEAK_G = 152 * 64 * 2.07 / 40
 
 
 # ----------------------------------------------------------------------------- workloads
@@ -120,6 +123,15 @@ class Workload:
             k = sum(1 for m in ("ic", "lt") if self.models.get(m) is not None)
             return k * self.seeds.size * 4, k * (self.trials * 4 + self.g.n * 4 + 8)
         return self.batch[1].size * 4, self.trials_per_step() * 4 + 8
+
+
+def select_models(wl: Workload, models: str) -> Workload:
+    keep = {m.strip() for m in models.split(",") if m.strip()}
+    if not keep <= {"ic", "lt"} or not keep:
+        raise SystemExit("--models takes ic, lt or ic,lt")
+    if wl.batch is None:
+        wl.models = {m: (d if m in keep else None) for m, d in wl.models.items()}
+    return wl
 
 
 def make_workload(name: str, trials: int = 0, items: int = 0) -> Workload:
@@ -314,7 +326,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = make_workload(args.workload, args.trials, args.items)
+    wl = select_models(make_workload(args.workload, args.trials, args.items), args.models)
     if args.ref_trials:
         for m, n in zip(("ic", "lt"), args.ref_trials):
             if m in wl.cpu:
@@ -435,6 +447,8 @@ def run_surrogate(args):
     tr = P.cnd_sur_train(sur, args.pairs, n_trials=T, batch_sets=16, sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1)
     train_s = time.perf_counter() - t0
     q1 = quality(sur)
+    print(f"trained {args.pairs} pairs in {train_s:.1f} s; held-out before {q0} after {q1}", file=sys.stderr,
+          flush=True)
 
     def judge(seeds):
         r = P.cnd_ic_simulate_ex(G, seeds, judge_T, judge_key, node_count=False)
@@ -446,6 +460,7 @@ def run_surrogate(args):
     rc = P.cnd_ic_im_celf(G, k, T, 1, graph=1)
     runs["mc_celf"] = {"s": time.perf_counter() - t0, "seeds": rc.seeds.tolist(), "evaluations": rc.evaluations,
                        "edge_checks": rc.edge_checks}
+    print(f"mc_celf: {runs['mc_celf']['s']:.2f} s", file=sys.stderr, flush=True)
     variants = (("screened_trained", sur, args.screen_mode), ("screened_trained_gradient", sur, "gradient"),
                 ("screened_trained_onehop", sur, "onehop"), ("screened_untrained", untrained, args.screen_mode),
                 ("screened_degree_no_network", None, "degree"))
@@ -457,6 +472,7 @@ def run_surrogate(args):
                                       graph=1)
         runs[name] = {"s": time.perf_counter() - t0, "mode": mode, "seeds": rs.seeds.tolist(),
                       "evaluations": rs.evaluations, "edge_checks": rs.edge_checks, **tm}
+        print(f"{name}: {runs[name]['s']:.2f} s", file=sys.stderr, flush=True)
     for v in runs.values():
         v["judged_spread"] = judge(v["seeds"])
     base = runs["mc_celf"]
@@ -489,7 +505,9 @@ KERNEL = {"ic": "k_push<0>", "lt": "k_push<1>"}
 
 
 def alg_bytes(model, s):
-    """Bytes the expansion kernel must move, from its own work counters (kernels)."""
+    """Bytes the expansion kernel must move, from its own work counters: 8 per work item (row_ptr pair),
+    8 per frontier word loaded, 8 per edge read ({col, thr}), 8 per word check (the target's word) and
+    16 per IC word update (vis and next read-modify-write) or 8 per LT accumulator add."""
     base = 8 * s["work_items"] + 8 * s["frontier_words"] + 8 * s["edges_scanned"] + 8 * s["word_checks"]
     return base + (16 if model == "ic" else 8) * s["updates"]
 
@@ -509,7 +527,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    wl = make_workload(args.workload, args.trials, args.items)
+    wl = select_models(make_workload(args.workload, args.trials, args.items), args.models)
     if wl.batch is not None and world > 1:
         # each rank its own seed sets: a disjoint slice of the 4096-item list
         g = wl.g
@@ -616,6 +634,19 @@ def run_ours(args):
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": ncu_traffic(K["kernel"], wl.name, wc_per_launch), "kernel": K["kernel"],
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
+    # the IC push draws a Philox-4x32-10 block (4 coins) per candidate 4-trial block: where its draws
+    # outweigh its bytes it is bound by integer multiplies, and its roofline is the Philox rate
+    alu = None
+    if "ic" in kern:
+        KI = kern["ic"]
+        draws_s = KI["counts"]["draws"] / args.steps / max(1e-9, KI["expand_ms_per_step"] * 1e-3)
+        alu = {"bound": "alu", "achieved": draws_s / 1e9, "peak": PHILOX_PEAK_G, "unit": "G Philox/s",
+               "frac": draws_s / 1e9 / PHILOX_PEAK_G, "kernel": KI["kernel"],
+               "peak_source": "derived: 152 SMs x 64 32-bit integer multiplies/clk x 2.07 GHz / 40 per Philox call",
+               "draws_per_word_check": KI["counts"]["draws"] / max(1, KI["counts"]["word_checks"])}
+        if dom == "ic" and alu["frac"] > roof["frac"]:
+            roof, alu = dict(alu, traffic=roof["traffic"], hbm_view={k: roof[k] for k in ("achieved", "peak",
+                                                                                     "unit", "frac")}), roof
 
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl)
     line = {
@@ -634,6 +665,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
+        "roofline_other": alu,
         "kernels": kern,
         "cpu_baseline": cpu,
         "wall_s_timed_region": wall,
@@ -651,6 +683,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ba100k",
                     choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7", "surrogate"])
+    ap.add_argument("--models", default="ic,lt", help="single-seed-set workloads: models to run (ic, lt or both)")
     ap.add_argument("--pairs", type=int, default=200_000, help="surrogate: training pairs")
     ap.add_argument("--k", type=int, default=50, help="surrogate: seeds to choose")
     ap.add_argument("--screen", type=int, default=64, help="surrogate: candidates kept by the gradient score")

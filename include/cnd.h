@@ -387,7 +387,8 @@ cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, double *loss_o
  *        (1 - yhat_c) (1 + sum over out-edges (c -> w) of q_e (1 - yhat_w));
  *      mode 2: out-degree (no network: the screen without the surrogate);
  *   2. if n_screen > n_exact, re-rank those by the surrogate's predicted
- *      spread of S + c (one forward each) and keep the n_exact best;
+ *      spread of S + c (one forward each) and keep the n_exact best (mode 2
+ *      keeps the n_exact best by out-degree directly; s may then be NULL);
  *   3. evaluate F(S + c) exactly for the survivors with the batched Monte
  *      Carlo engine (common random numbers as in CELF: trials first_trial ..
  *      first_trial + n_trials - 1 of key rng_seed) and choose the best

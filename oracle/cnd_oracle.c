@@ -23,7 +23,7 @@
  *   (IC) / recomputes every node's active in-weight (LT) at every step, the
  *   per-step whole-graph loop the paper attributes to NDlib (Sec. 1).
  *
- * Readings fixed where the paper is silent or ambiguous (listed in the design doc):
+ * Readings fixed where the paper is silent or ambiguous:
  *   R1 random numbers: Philox4x32-10 (Salmon et al., SC'11), key =
  *      (lo32(rng_seed), hi32(rng_seed)).  For trial t (g = t >> 2, j = t & 3):
  *        IC coin of edge e   = philox(e, lo32(g), 0, hi32(g))[j]

@@ -336,7 +336,8 @@ cnd_status screened(const cnd_graph *g, cnd_sur *sur, const cnd_im_opts *o, cons
                 pool.push_back(v);
                 val.push_back((double)score[(size_t)v]);
             }
-        std::vector<int32_t> keep = top_by(pool, val, n_screen);
+        // without a network (mode 2) the first score alone picks the candidates to simulate
+        std::vector<int32_t> keep = top_by(pool, val, so->mode == 2 ? n_exact : n_screen);
         if (keep.size() > n_exact) {
             val.assign(keep.size(), 0.0);
             for (size_t i = 0; i < keep.size(); ++i) {

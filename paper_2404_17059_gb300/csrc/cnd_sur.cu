@@ -1237,13 +1237,23 @@ extern "C" cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, dou
         set_error("cnd_sur_train: alloc counts: %s", cudaGetErrorString(e));
         return CND_ENOMEM;
     }
+    double *d_loss = nullptr;
+    e = cudaMalloc(&d_loss, sizeof(double) * (size_t)((chunk + B - 1) / B));
+    if (e != cudaSuccess) {
+        cudaFree(d_seeds);
+        cudaFree(d_cnt);
+        set_error("cnd_sur_train: alloc: %s", cudaGetErrorString(e));
+        return CND_ENOMEM;
+    }
     struct Free {
         int32_t *a, *b;
+        double *c;
         ~Free() {
             cudaFree(a);
             cudaFree(b);
+            cudaFree(c);
         }
-    } fr{d_seeds, d_cnt};
+    } fr{d_seeds, d_cnt, d_loss};
     std::vector<int32_t> hs, one;
     std::vector<int64_t> off;
     std::vector<int32_t> trials;
@@ -1274,7 +1284,8 @@ extern "C" cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, dou
         if (st != CND_OK) return st;
         CND_CUDA_TRY(cudaStreamSynchronize(cs));
         const auto t1 = std::chrono::steady_clock::now();
-        // the seed lists of the simulator are the caller's (duplicates impossible: distinct draws)
+        // seed lists hold distinct nodes by construction; a step's loss is kept on the device
+        const int64_t step0 = step;
         for (int32_t b0 = 0; b0 < cnt; b0 += B) {
             const int32_t nb = std::min(B, cnt - b0);
             CND_CUDA_TRY(cudaMemsetAsync(s->grad, 0, sizeof(float) * N_PARAMS, cs));
@@ -1294,11 +1305,13 @@ extern "C" cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, dou
                                                                         c1, c2);
             pack_weights(s, cs);
             CND_CUDA_TRY(cudaGetLastError());
-            if (loss_out) {
-                CND_CUDA_TRY(cudaMemcpyAsync(loss_out + step, s->dsum + 1, sizeof(double), cudaMemcpyDeviceToHost, cs));
-            }
+            CND_CUDA_TRY(cudaMemcpyAsync(d_loss + (step - step0), s->dsum + 1, sizeof(double), cudaMemcpyDeviceToDevice,
+                                         cs));
             ++step;
         }
+        if (loss_out)
+            CND_CUDA_TRY(cudaMemcpyAsync(loss_out + step0, d_loss, sizeof(double) * (size_t)(step - step0),
+                                         cudaMemcpyDeviceToHost, cs));
         CND_CUDA_TRY(cudaStreamSynchronize(cs));
         const auto t2 = std::chrono::steady_clock::now();
         sim_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();

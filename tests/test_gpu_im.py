@@ -94,3 +94,11 @@ def test_screened_greedy_values_are_exact(er0):
     for j in range(5):
         ref = oracle.simulate("ic", g, r.seeds[:j + 1], 128, 3, ic_prob=p, level_counts_len=0)
         assert r.f[j] == int(ref.spread.astype(np.int64).sum())
+
+
+def test_screened_greedy_degree_mode_needs_no_network(er0):
+    g, G, p, _ = er0
+    r, tm = P.cnd_ic_im_screened(G, None, 3, 128, 5, n_screen=16, n_exact=2, mode="degree")
+    deg = np.diff(g.row_ptr)
+    assert r.seeds[0] in np.argsort(-deg, kind="stable")[:2]
+    assert r.evaluations == 3 * 2 and tm["sur_ms"] >= 0
