@@ -112,7 +112,7 @@ typedef struct cnd_sim_opts {
                                   (outputs are still written) */
     int32_t direction;         /* CND_DIR_* */
     int32_t word_bits;         /* trials held per node per pass: 0 = automatic, else a multiple
-                                  of 64 up to 16384 */
+                                  of 64 up to 131072 (pulling passes hold at most 16384) */
     int32_t device_ptrs;       /* 1: seeds and all outputs are device pointers; the work runs
                                   on `stream`, and the call returns once it is complete */
     void *stream;              /* cudaStream_t to run on; NULL = legacy default stream */

@@ -46,7 +46,9 @@
 
 namespace cnd {
 
-constexpr int kMaxB = 256;   // words per node per pass
+constexpr int kMaxB = 2048;  // words per node per pass (dirty mask: one 64-bit word per lane)
+constexpr int kStageB = 256; // pairs of a push work item staged in shared memory (more: read from the pool)
+constexpr int kPullMaxB = 256;  // words per node the pull kernel keeps in registers
 constexpr int kTasks = 256;  // (edge, pair) tasks per push work item
 // AUTO without pull_permille: push only -- the pull step measured 1.3x to 3.7x
 // slower than push on every GB300 workload here (hub in-rows scanned by one warp)
@@ -248,15 +250,19 @@ __global__ void k_seed(Params p_, const SeedSeg *__restrict__ segs, int32_t n_se
 }
 
 // ---------------------------------------------------------------- finalize
-// Word index of the r-th word listed in a node's dirty mask (nq <= 4 words).
-__device__ __forceinline__ int word_at(const uint64_t (&dm)[4], int r) {
+// Word index of the r-th word listed in a node's dirty mask.  Lane q holds mask word q
+// (nq <= 32) in `mine` and the inclusive count of listed words up to it in `incl`; each
+// lane asks for its own r (0 <= r < listed words), so every lane must call this.
+__device__ __forceinline__ int word_at(uint64_t mine, int incl, int r) {
+    int q = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int c = __popcll(dm[q]);
-        if (r < c) return 64 * q + nth_set_bit(dm[q], r);
-        r -= c;
+    for (int step = 16; step >= 1; step >>= 1) {
+        const int x = __shfl_sync(kFull, incl, q + step - 1);
+        if (x <= r) q += step;
     }
-    return 0;
+    const uint64_t wq = __shfl_sync(kFull, mine, q);
+    const int before = __shfl_sync(kFull, incl, q) - __popcll(wq);
+    return 64 * q + nth_set_bit(wq, r - before);
 }
 
 // Placement of the slots of the nodes a block finalizes together: a block
@@ -294,23 +300,23 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p_) {
     unsigned long long pc = 0;
     uint32_t n_dr = 0;
     for (int base = blockIdx.x * kNPB; base < count; base += gridDim.x * kNPB) {
-        int vv[kNPW], KK[kNPW];
-        uint64_t dm[kNPW][4];
+        int vv[kNPW], KK[kNPW], dinc[kNPW];
+        uint64_t dmine[kNPW];
 #pragma unroll
         for (int h = 0; h < kNPW; ++h) {
             const int i = base + wid * kNPW + h;
             const bool act = i < count;
             vv[h] = act ? p.lin[i] : 0;
-            KK[h] = 0;
-            dm[h][0] = dm[h][1] = dm[h][2] = dm[h][3] = 0ull;
-            if (!act) continue;
-            const uint64_t mine = (lane < nq) ? p.dmask[(size_t)vv[h] * nq + lane] : 0ull;
-            if (lane < nq) p.dmask[(size_t)vv[h] * nq + lane] = 0ull;
+            dmine[h] = (act && lane < nq) ? p.dmask[(size_t)vv[h] * nq + lane] : 0ull;
+            if (act && lane < nq) p.dmask[(size_t)vv[h] * nq + lane] = 0ull;
+            int c = __popcll(dmine[h]);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                dm[h][q] = __shfl_sync(kFull, mine, q);
-                KK[h] += __popcll(dm[h][q]);
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(kFull, c, o);
+                if (lane >= o) c += x;
             }
+            dinc[h] = c;
+            KK[h] = __shfl_sync(kFull, c, 31);
         }
 #pragma unroll
         for (int h = 0; h < kNPW; ++h) {
@@ -323,9 +329,8 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p_) {
                 for (int r0 = 0; r0 < K; r0 += 32) {
                     const int r = r0 + lane;
                     uint64_t nb = 0;
-                    int w = 0;
+                    const int w = word_at(dmine[h], dinc[h], min(r, K - 1));
                     if (r < K) {
-                        w = word_at(dm[h], r);
                         const size_t idx = (size_t)v * B + w;
                         const uint64_t x = p.nxt[idx];
                         if (MODE == 1) {
@@ -443,9 +448,8 @@ __global__ void __launch_bounds__(kBlock) k_finalize(Params p_) {
             for (int r0 = 0; r0 < K; r0 += 32) {
                 const int r = r0 + lane;
                 uint64_t x = 0;
-                int w = 0;
+                const int w = word_at(dmine[h], dinc[h], min(r, K - 1));
                 if (r < K) {
-                    w = word_at(dm[h], r);
                     const size_t idx = (size_t)v * B + w;
                     x = p.nxt[idx];
                     // a word that waits got its dirty bit back in the pass above
@@ -498,8 +502,8 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p_) {
     Params p = p_;
     resolve(p);
     if (p.ctl && p.ctl->pull) return;  // graph mode: this step pulls
-    __shared__ uint64_t s_b[kWarps][kMaxB];
-    __shared__ uint16_t s_w[kWarps][kMaxB];
+    __shared__ uint64_t s_b[kWarps][kStageB];
+    __shared__ uint16_t s_w[kWarps][kStageB];
     __shared__ int32_t s_list[kWarps][64];
     __shared__ DrawQueue s_dq[MODEL == 0 ? kWarps : 1];
     const int lane = lane_id();
@@ -520,10 +524,12 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p_) {
         const int ne = edges_per_item(p, k);
         const int e_begin = row0 + it.y;
         const int e_cnt = min(ne, deg - it.y);
-        for (int j = lane; j < k; j += 32) {
-            s_b[wid][j] = p.in.pb[off + j];
-            s_w[wid][j] = p.in.pw[off + j];
-        }
+        const bool staged = k <= kStageB;
+        if (staged)
+            for (int j = lane; j < k; j += 32) {
+                s_b[wid][j] = p.in.pb[off + j];
+                s_w[wid][j] = p.in.pw[off + j];
+            }
         __syncwarp();
         if (lane == 0) {
             n_edges += e_cnt;
@@ -545,8 +551,8 @@ __global__ void __launch_bounds__(kBlock) k_push(Params p_) {
                 const int e = e_begin + (int)el;
                 const uint2 ed = __ldg(&p.edge[e]);
                 v = (int)ed.x;
-                const int w = s_w[wid][j];
-                const uint64_t f = s_b[wid][j];
+                const int w = staged ? (int)s_w[wid][j] : (int)p.in.pw[off + j];
+                const uint64_t f = staged ? s_b[wid][j] : p.in.pb[off + j];
                 const size_t idx = (size_t)v * B + w;
                 if (MODEL == 0) {
                     ic_c = 0;
@@ -725,7 +731,7 @@ __global__ void __launch_bounds__(kBlock) k_pull_ic(Params p_) {
     Params p = p_;
     resolve(p);
     if (p.ctl && !p.ctl->pull) return;
-    constexpr int NW = kMaxB / 32;
+    constexpr int NW = kPullMaxB / 32;
     __shared__ int32_t s_list[kWarps][64];
     const int lane = lane_id();
     const int wid = threadIdx.x >> 5;
@@ -1052,9 +1058,12 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     const double budget = 0.6 * (double)free_b;
     // bytes per word column: vis, nxt, two pair pools (+ LT accumulators)
     const double per_word = (double)n * (2 * 8 + 2 * 10 + (model == 1 ? 256 : 0));
+    // pulling (IC) happens only when asked for: by direction, or by a switch threshold
+    const bool may_pull = model == 0 && G.m > 0 &&
+                          (o.direction == CND_DIR_PULL || (o.direction == CND_DIR_AUTO && o.pull_permille > 0));
     int64_t bmax = o.word_bits ? o.word_bits / 64 : kMaxB;
     bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)(budget / per_word)));
-    bmax = std::min<int64_t>(bmax, kMaxB);
+    bmax = std::min<int64_t>(bmax, may_pull ? kPullMaxB : kMaxB);
     bmax = std::min<int64_t>(bmax, std::max<int64_t>(1, (int64_t)0x7FFFFFFF / std::max(n, 1)));
     const int64_t n_pass = (total_words + bmax - 1) / bmax;
     const int B = (int)((total_words + n_pass - 1) / n_pass);
@@ -1181,7 +1190,6 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
         CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
     }
     // pull direction (IC only): node-indexed frontier and frontier-node bitmap
-    const bool may_pull = model == 0 && o.direction != CND_DIR_PUSH && G.m > 0;
     const int permille = o.pull_permille > 0 ? o.pull_permille : kPullPermille;
     if (may_pull) {
         CND_CUDA_TRY(W.alloc(&P.fdense, nB));

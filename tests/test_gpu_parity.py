@@ -120,6 +120,32 @@ def test_word_widths_and_chunks(er0, model):
 
 
 @pytest.mark.parametrize("model", ["ic", "lt"])
+def test_wide_passes(er0, model):
+    """Passes wider than 256 words: dirty masks of more than 4 words (up to 32) and push items
+    with more frontier words than a warp stages in shared memory."""
+    g, G, p, w, seeds = er0
+    b = ref(model, g, seeds, 40_000, 12, p=p, w=w)  # 625 words
+    for wb in (0, 64 * 625, 64 * 300, 64 * 2048):
+        assert_same(sim(model, G, seeds, 40_000, 12, word_bits=wb), b)
+    assert_same(sim(model, G, seeds, 40_000, 12, chunk_edges=2), b)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_wide_batch_passes(rmat14, model):
+    """Many small items in one pass of up to 2048 words."""
+    g, G, p, w, _ = rmat14
+    seed_off, seeds, trials, keys = I.batch_items(g.n, 150, 1, 30, (64, 128, 1000, 640), graph_seed=8)
+    f = P.cnd_ic_simulate_batch if model == "ic" else P.cnd_lt_simulate_batch
+    want_sp, want_nc, want_ck = _batch_ref(model, g, p, w, seed_off, seeds, trials, keys)
+    for wb in (0, 64 * 1500):
+        a = f(G, seed_off, seeds, trials, keys, node_count=True, edge_checks=True, word_bits=wb, stats=1)
+        assert np.array_equal(a.spread, want_sp)
+        assert np.array_equal(a.node_count, want_nc)
+        assert a.edge_checks == want_ck
+        assert a.stats["word_bits"] > 64 * 256
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
 def test_ragged_trial_counts(ba, model):
     g, G, p, w, seeds = ba
     for T in (1, 3, 63, 64, 65, 130, 257):
