@@ -184,54 +184,64 @@ struct Item {
     int32_t node, begin, end, slot;  // slot >= 0: partial row of a split node (scratch row index)
 };
 
-// a[v] = bf16(sum over in-edges of q h[src]) for 64-wide bf16 rows; a warp per item
+// a[v] = bf16(sum over in-edges of q h[src]) for 64-wide bf16 rows; a warp per item.  The warp
+// gathers 4 rows per load instruction (8 lanes x 16 B per 128-byte row), 8 rows in flight, and
+// folds the 4 partial sums of each feature at the end.
 __global__ void __launch_bounds__(256) k_spmm_in(int32_t n_items, const Item *__restrict__ items,
                                                  const uint2 *__restrict__ in_c, const __nv_bfloat16 *__restrict__ h,
                                                  __nv_bfloat16 *__restrict__ a, float *__restrict__ scratch) {
     const int lane = threadIdx.x & 31;
+    const int sub = lane >> 3;       // which of 4 edges
+    const int f8 = (lane & 7) * 8;   // first of this lane's 8 features
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int it = warp; it < n_items; it += nwarps) {
         const Item item = items[it];
-        float s0 = 0.0f, s1 = 0.0f;
+        float acc[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = 0.0f;
         for (int32_t b = item.begin; b < item.end; b += 32) {
             const int cnt = min(32, item.end - b);
             uint2 my = make_uint2(0u, 0u);
             if (lane < cnt) my = in_c[b + lane];
             const float myq = edge_q(my.y);
-            int j = 0;
-            for (; j + 4 <= cnt; j += 4) {
-                const uint32_t u0 = __shfl_sync(0xffffffffu, my.x, j), u1 = __shfl_sync(0xffffffffu, my.x, j + 1);
-                const uint32_t u2 = __shfl_sync(0xffffffffu, my.x, j + 2), u3 = __shfl_sync(0xffffffffu, my.x, j + 3);
-                const float q0 = __shfl_sync(0xffffffffu, myq, j), q1 = __shfl_sync(0xffffffffu, myq, j + 1);
-                const float q2 = __shfl_sync(0xffffffffu, myq, j + 2), q3 = __shfl_sync(0xffffffffu, myq, j + 3);
-                const uint32_t r0 = ld_u32(h + (size_t)u0 * H + 2 * lane);
-                const uint32_t r1 = ld_u32(h + (size_t)u1 * H + 2 * lane);
-                const uint32_t r2 = ld_u32(h + (size_t)u2 * H + 2 * lane);
-                const uint32_t r3 = ld_u32(h + (size_t)u3 * H + 2 * lane);
-                const float2 f0 = unpack_bf16(r0), f1 = unpack_bf16(r1), f2 = unpack_bf16(r2), f3 = unpack_bf16(r3);
-                s0 += q0 * f0.x;
-                s1 += q0 * f0.y;
-                s0 += q1 * f1.x;
-                s1 += q1 * f1.y;
-                s0 += q2 * f2.x;
-                s1 += q2 * f2.y;
-                s0 += q3 * f3.x;
-                s1 += q3 * f3.y;
-            }
-            for (; j < cnt; ++j) {
-                const uint32_t u = __shfl_sync(0xffffffffu, my.x, j);
-                const float q = __shfl_sync(0xffffffffu, myq, j);
-                const float2 f = unpack_bf16(ld_u32(h + (size_t)u * H + 2 * lane));
-                s0 += q * f.x;
-                s1 += q * f.y;
+            for (int j = 0; j < cnt; j += 8) {
+                // edges j + sub and j + 4 + sub (q = 0 past the end: row 0 read, nothing added)
+                const int e0 = j + sub, e1 = j + 4 + sub;
+                const uint32_t u0 = __shfl_sync(0xffffffffu, my.x, e0 & 31);
+                const uint32_t u1 = __shfl_sync(0xffffffffu, my.x, e1 & 31);
+                float q0 = __shfl_sync(0xffffffffu, myq, e0 & 31);
+                float q1 = __shfl_sync(0xffffffffu, myq, e1 & 31);
+                if (e0 >= cnt) q0 = 0.0f;
+                if (e1 >= cnt) q1 = 0.0f;
+                const uint4 r0 = *reinterpret_cast<const uint4 *>(h + (size_t)(e0 < cnt ? u0 : 0u) * H + f8);
+                const uint4 r1 = *reinterpret_cast<const uint4 *>(h + (size_t)(e1 < cnt ? u1 : 0u) * H + f8);
+                const uint32_t w0[4] = {r0.x, r0.y, r0.z, r0.w}, w1[4] = {r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float2 x0 = unpack_bf16(w0[i]), x1 = unpack_bf16(w1[i]);
+                    acc[2 * i] += q0 * x0.x + q1 * x1.x;
+                    acc[2 * i + 1] += q0 * x0.y + q1 * x1.y;
+                }
             }
         }
-        if (item.slot < 0) {
-            *reinterpret_cast<uint32_t *>(a + (size_t)item.node * H + 2 * lane) = pack_bf16(s0, s1);
-        } else {
-            atomicAdd(scratch + (size_t)item.slot * H + 2 * lane, s0);
-            atomicAdd(scratch + (size_t)item.slot * H + 2 * lane + 1, s1);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 8);
+            acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], 16);
+        }
+        if (lane < 8) {
+            if (item.slot < 0) {
+                uint4 o;
+                o.x = pack_bf16(acc[0], acc[1]);
+                o.y = pack_bf16(acc[2], acc[3]);
+                o.z = pack_bf16(acc[4], acc[5]);
+                o.w = pack_bf16(acc[6], acc[7]);
+                *reinterpret_cast<uint4 *>(a + (size_t)item.node * H + f8) = o;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) atomicAdd(scratch + (size_t)item.slot * H + f8 + i, acc[i]);
+            }
         }
     }
 }
@@ -250,58 +260,61 @@ __global__ void k_split_finish(int32_t n_split, const int32_t *__restrict__ spli
     }
 }
 
-// dh[u] += sum over out-edges (u -> w) of q da[w], 64-wide fp32 rows; a warp per item of the out-CSR.
-// Items of a split node add with atomics; a single-item node is read-modify-written by its warp.
+// dh[u] += sum over out-edges (u -> w) of q da[w], 64-wide fp32 rows; a warp per item of the out-CSR,
+// 2 rows per load instruction (16 lanes x 16 B per 256-byte row), 4 rows in flight.  Items of a
+// split node add with atomics; a single-item node is read-modify-written by its warp.
 __global__ void __launch_bounds__(256) k_spmm_out(int32_t n_items, const Item *__restrict__ items,
                                                   const uint2 *__restrict__ ic_edge, const float *__restrict__ da,
                                                   float *__restrict__ dh) {
     const int lane = threadIdx.x & 31;
+    const int sub = lane >> 4;       // which of 2 edges
+    const int f4 = (lane & 15) * 4;  // first of this lane's 4 features
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int it = warp; it < n_items; it += nwarps) {
         const Item item = items[it];
-        float s0 = 0.0f, s1 = 0.0f;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int32_t b = item.begin; b < item.end; b += 32) {
             const int cnt = min(32, item.end - b);
             uint2 my = make_uint2(0u, 0u);
             if (lane < cnt) my = ic_edge[b + lane];
             const float myq = edge_q(my.y);
-            int j = 0;
-            for (; j + 4 <= cnt; j += 4) {
-                const uint32_t w0 = __shfl_sync(0xffffffffu, my.x, j), w1 = __shfl_sync(0xffffffffu, my.x, j + 1);
-                const uint32_t w2 = __shfl_sync(0xffffffffu, my.x, j + 2), w3 = __shfl_sync(0xffffffffu, my.x, j + 3);
-                const float q0 = __shfl_sync(0xffffffffu, myq, j), q1 = __shfl_sync(0xffffffffu, myq, j + 1);
-                const float q2 = __shfl_sync(0xffffffffu, myq, j + 2), q3 = __shfl_sync(0xffffffffu, myq, j + 3);
-                const float2 f0 = reinterpret_cast<const float2 *>(da + (size_t)w0 * H)[lane];
-                const float2 f1 = reinterpret_cast<const float2 *>(da + (size_t)w1 * H)[lane];
-                const float2 f2 = reinterpret_cast<const float2 *>(da + (size_t)w2 * H)[lane];
-                const float2 f3 = reinterpret_cast<const float2 *>(da + (size_t)w3 * H)[lane];
-                s0 += q0 * f0.x;
-                s1 += q0 * f0.y;
-                s0 += q1 * f1.x;
-                s1 += q1 * f1.y;
-                s0 += q2 * f2.x;
-                s1 += q2 * f2.y;
-                s0 += q3 * f3.x;
-                s1 += q3 * f3.y;
-            }
-            for (; j < cnt; ++j) {
-                const uint32_t w = __shfl_sync(0xffffffffu, my.x, j);
-                const float q = __shfl_sync(0xffffffffu, myq, j);
-                const float2 f = reinterpret_cast<const float2 *>(da + (size_t)w * H)[lane];
-                s0 += q * f.x;
-                s1 += q * f.y;
+            for (int j = 0; j < cnt; j += 4) {
+                const int e0 = j + sub, e1 = j + 2 + sub;
+                const uint32_t w0 = __shfl_sync(0xffffffffu, my.x, e0 & 31);
+                const uint32_t w1 = __shfl_sync(0xffffffffu, my.x, e1 & 31);
+                float q0 = __shfl_sync(0xffffffffu, myq, e0 & 31);
+                float q1 = __shfl_sync(0xffffffffu, myq, e1 & 31);
+                if (e0 >= cnt) q0 = 0.0f;
+                if (e1 >= cnt) q1 = 0.0f;
+                const float4 x0 = *reinterpret_cast<const float4 *>(da + (size_t)(e0 < cnt ? w0 : 0u) * H + f4);
+                const float4 x1 = *reinterpret_cast<const float4 *>(da + (size_t)(e1 < cnt ? w1 : 0u) * H + f4);
+                acc.x += q0 * x0.x + q1 * x1.x;
+                acc.y += q0 * x0.y + q1 * x1.y;
+                acc.z += q0 * x0.z + q1 * x1.z;
+                acc.w += q0 * x0.w + q1 * x1.w;
             }
         }
-        float2 *row = reinterpret_cast<float2 *>(dh + (size_t)item.node * H);
-        if (item.slot < 0) {
-            float2 v = row[lane];
-            v.x += s0;
-            v.y += s1;
-            row[lane] = v;
-        } else {
-            atomicAdd(&row[lane].x, s0);
-            atomicAdd(&row[lane].y, s1);
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+        acc.z += __shfl_xor_sync(0xffffffffu, acc.z, 16);
+        acc.w += __shfl_xor_sync(0xffffffffu, acc.w, 16);
+        if (lane < 16) {
+            float4 *row = reinterpret_cast<float4 *>(dh + (size_t)item.node * H + f4);
+            if (item.slot < 0) {
+                float4 v = *row;
+                v.x += acc.x;
+                v.y += acc.y;
+                v.z += acc.z;
+                v.w += acc.w;
+                *row = v;
+            } else {
+                float *r = dh + (size_t)item.node * H + f4;
+                atomicAdd(r, acc.x);
+                atomicAdd(r + 1, acc.y);
+                atomicAdd(r + 2, acc.z);
+                atomicAdd(r + 3, acc.w);
+            }
         }
     }
 }
@@ -527,7 +540,9 @@ __global__ void __launch_bounds__(128) k_dense_bwd(int32_t n, const __nv_bfloat1
         }
     }
     if (GRADS) {
-        // reduce over the 8 row groups (lanes with equal t), then one atomic per column per warp
+        // reduce over the 8 row groups (lanes with equal t), then over the block's warps in shared
+        // memory, then one atomic per column per block
+        __shared__ float s_db[4][H], s_dwo[4][H], s_misc[4][2];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
             for (int off = 4; off < 32; off <<= 1) {
@@ -535,16 +550,15 @@ __global__ void __launch_bounds__(128) k_dense_bwd(int32_t n, const __nv_bfloat1
                 if (MODE == 1) dwo[i] += __shfl_xor_sync(0xffffffffu, dwo[i], off);
             }
         }
+        const int wib = threadIdx.x >> 5;
         if (g == 0) {
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 const int col = j * 8 + 2 * t;
-                atomicAdd(grad + off_b(layer) + col, db[2 * j]);
-                atomicAdd(grad + off_b(layer) + col + 1, db[2 * j + 1]);
-                if (MODE == 1) {
-                    atomicAdd(grad + OFF_WO + col, dwo[2 * j]);
-                    atomicAdd(grad + OFF_WO + col + 1, dwo[2 * j + 1]);
-                }
+                s_db[wib][col] = db[2 * j];
+                s_db[wib][col + 1] = db[2 * j + 1];
+                s_dwo[wib][col] = dwo[2 * j];
+                s_dwo[wib][col + 1] = dwo[2 * j + 1];
             }
         }
         if (MODE == 1) {
@@ -553,9 +567,29 @@ __global__ void __launch_bounds__(128) k_dense_bwd(int32_t n, const __nv_bfloat1
                 lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
             }
             if (lane == 0) {
-                atomicAdd(grad + OFF_BO, dbo);
-                atomicAdd(ha.loss, (double)lsum * (double)ha.loss_scale);
+                s_misc[wib][0] = dbo;
+                s_misc[wib][1] = lsum;
             }
+        }
+        __syncthreads();
+        const int nw = blockDim.x >> 5;
+        if (threadIdx.x < H) {
+            float a = 0.0f, b = 0.0f;
+            for (int w = 0; w < nw; ++w) {
+                a += s_db[w][threadIdx.x];
+                b += s_dwo[w][threadIdx.x];
+            }
+            atomicAdd(grad + off_b(layer) + threadIdx.x, a);
+            if (MODE == 1) atomicAdd(grad + OFF_WO + threadIdx.x, b);
+        }
+        if (MODE == 1 && threadIdx.x == 0) {
+            float a = 0.0f, b = 0.0f;
+            for (int w = 0; w < nw; ++w) {
+                a += s_misc[w][0];
+                b += s_misc[w][1];
+            }
+            atomicAdd(grad + OFF_BO, a);
+            atomicAdd(ha.loss, (double)b * (double)ha.loss_scale);
         }
     }
 }
@@ -834,18 +868,19 @@ void aggregate_out(cnd_sur *s, const float *da, float *dh, cudaStream_t st) {
 void backward_loss(cnd_sur *s, const float *y, const int32_t *cnt, float inv_t, float batch, cudaStream_t st) {
     const int32_t n = s->n;
     const int tb = grid_for(((int64_t)n + 15) / 16 * 32, 128, s->num_sms, 16);
+    const int tbb = grid_for(((int64_t)n + 15) / 16 * 32, 128, s->num_sms, 4);  // backward: few blocks, few atomics
     const int rpb = (int)std::max<int64_t>(512, (((int64_t)n + 2 * s->num_sms - 1) / (2 * s->num_sms) + 31) / 32 * 32);
     const int db = (int)std::max<int64_t>(1, ((int64_t)n + rpb - 1) / rpb);
     HeadArgs ha{s->o, s->x, y, cnt, inv_t, 2.0f / (float)n / batch, s->dsum + 1, 1.0f / (float)n / batch};
     HeadArgs none{};
     __nv_bfloat16 *wt2 = s->wt + 64 * 32 + 64 * 128, *wt1 = s->wt + 64 * 32;
-    k_dense_bwd<H, 1, 1, true><<<tb, 128, 0, st>>>(n, s->h[2], nullptr, ha, wt2, 2, s->p, s->e, s->dhA, s->da, s->grad);
+    k_dense_bwd<H, 1, 1, true><<<tbb, 128, 0, st>>>(n, s->h[2], nullptr, ha, wt2, 2, s->p, s->e, s->dhA, s->da, s->grad);
     k_dw<H><<<db, 256, 0, st>>>(n, s->e, s->h[1], s->a[2], 2, s->grad, rpb);
     aggregate_out(s, s->da, s->dhA, st);
-    k_dense_bwd<H, 0, 1, true><<<tb, 128, 0, st>>>(n, s->h[1], s->dhA, none, wt1, 1, s->p, s->e, s->dhB, s->da, s->grad);
+    k_dense_bwd<H, 0, 1, true><<<tbb, 128, 0, st>>>(n, s->h[1], s->dhA, none, wt1, 1, s->p, s->e, s->dhB, s->da, s->grad);
     k_dw<H><<<db, 256, 0, st>>>(n, s->e, s->h[0], s->a[1], 1, s->grad, rpb);
     aggregate_out(s, s->da, s->dhB, st);
-    k_dense_bwd<D0, 0, 0, true><<<tb, 128, 0, st>>>(n, s->h[0], s->dhB, none, s->wt, 0, s->p, s->e, nullptr, nullptr,
+    k_dense_bwd<D0, 0, 0, true><<<tbb, 128, 0, st>>>(n, s->h[0], s->dhB, none, s->wt, 0, s->p, s->e, nullptr, nullptr,
                                                      s->grad);
     k_dw<D0><<<db, 256, 0, st>>>(n, s->e, s->x, s->a1, 0, s->grad, rpb);
 }
