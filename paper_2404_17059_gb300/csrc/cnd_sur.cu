@@ -185,7 +185,7 @@ struct Item {
 };
 
 // a[v] = bf16(sum over in-edges of q h[src]) for 64-wide bf16 rows; a warp per item.  The warp
-// gathers 4 rows per load instruction (8 lanes x 16 B per 128-byte row), 8 rows in flight, and
+// gathers 4 rows per load instruction (8 lanes x 16 B per 128-byte row), 16 rows in flight, and
 // folds the 4 partial sums of each feature at the end.
 __global__ void __launch_bounds__(256) k_spmm_in(int32_t n_items, const Item *__restrict__ items,
                                                  const uint2 *__restrict__ in_c, const __nv_bfloat16 *__restrict__ h,
@@ -205,23 +205,27 @@ __global__ void __launch_bounds__(256) k_spmm_in(int32_t n_items, const Item *__
             uint2 my = make_uint2(0u, 0u);
             if (lane < cnt) my = in_c[b + lane];
             const float myq = edge_q(my.y);
-            for (int j = 0; j < cnt; j += 8) {
-                // edges j + sub and j + 4 + sub (q = 0 past the end: row 0 read, nothing added)
-                const int e0 = j + sub, e1 = j + 4 + sub;
-                const uint32_t u0 = __shfl_sync(0xffffffffu, my.x, e0 & 31);
-                const uint32_t u1 = __shfl_sync(0xffffffffu, my.x, e1 & 31);
-                float q0 = __shfl_sync(0xffffffffu, myq, e0 & 31);
-                float q1 = __shfl_sync(0xffffffffu, myq, e1 & 31);
-                if (e0 >= cnt) q0 = 0.0f;
-                if (e1 >= cnt) q1 = 0.0f;
-                const uint4 r0 = *reinterpret_cast<const uint4 *>(h + (size_t)(e0 < cnt ? u0 : 0u) * H + f8);
-                const uint4 r1 = *reinterpret_cast<const uint4 *>(h + (size_t)(e1 < cnt ? u1 : 0u) * H + f8);
-                const uint32_t w0[4] = {r0.x, r0.y, r0.z, r0.w}, w1[4] = {r1.x, r1.y, r1.z, r1.w};
+            for (int j = 0; j < cnt; j += 16) {
+                // edges j + sub + 4 r, r = 0..3 (q = 0 past the end: row 0 read, nothing added)
+                uint4 rr[4];
+                float qq[4];
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float2 x0 = unpack_bf16(w0[i]), x1 = unpack_bf16(w1[i]);
-                    acc[2 * i] += q0 * x0.x + q1 * x1.x;
-                    acc[2 * i + 1] += q0 * x0.y + q1 * x1.y;
+                for (int r = 0; r < 4; ++r) {
+                    const int e = j + sub + 4 * r;
+                    const uint32_t u = __shfl_sync(0xffffffffu, my.x, e & 31);
+                    const float q = __shfl_sync(0xffffffffu, myq, e & 31);
+                    qq[r] = e < cnt ? q : 0.0f;
+                    rr[r] = *reinterpret_cast<const uint4 *>(h + (size_t)(e < cnt ? u : 0u) * H + f8);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const uint32_t w4[4] = {rr[r].x, rr[r].y, rr[r].z, rr[r].w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 x = unpack_bf16(w4[i]);
+                        acc[2 * i] += qq[r] * x.x;
+                        acc[2 * i + 1] += qq[r] * x.y;
+                    }
                 }
             }
         }
@@ -261,7 +265,7 @@ __global__ void k_split_finish(int32_t n_split, const int32_t *__restrict__ spli
 }
 
 // dh[u] += sum over out-edges (u -> w) of q da[w], 64-wide fp32 rows; a warp per item of the out-CSR,
-// 2 rows per load instruction (16 lanes x 16 B per 256-byte row), 4 rows in flight.  Items of a
+// 2 rows per load instruction (16 lanes x 16 B per 256-byte row), 8 rows in flight.  Items of a
 // split node add with atomics; a single-item node is read-modify-written by its warp.
 __global__ void __launch_bounds__(256) k_spmm_out(int32_t n_items, const Item *__restrict__ items,
                                                   const uint2 *__restrict__ ic_edge, const float *__restrict__ da,
@@ -279,20 +283,24 @@ __global__ void __launch_bounds__(256) k_spmm_out(int32_t n_items, const Item *_
             uint2 my = make_uint2(0u, 0u);
             if (lane < cnt) my = ic_edge[b + lane];
             const float myq = edge_q(my.y);
-            for (int j = 0; j < cnt; j += 4) {
-                const int e0 = j + sub, e1 = j + 2 + sub;
-                const uint32_t w0 = __shfl_sync(0xffffffffu, my.x, e0 & 31);
-                const uint32_t w1 = __shfl_sync(0xffffffffu, my.x, e1 & 31);
-                float q0 = __shfl_sync(0xffffffffu, myq, e0 & 31);
-                float q1 = __shfl_sync(0xffffffffu, myq, e1 & 31);
-                if (e0 >= cnt) q0 = 0.0f;
-                if (e1 >= cnt) q1 = 0.0f;
-                const float4 x0 = *reinterpret_cast<const float4 *>(da + (size_t)(e0 < cnt ? w0 : 0u) * H + f4);
-                const float4 x1 = *reinterpret_cast<const float4 *>(da + (size_t)(e1 < cnt ? w1 : 0u) * H + f4);
-                acc.x += q0 * x0.x + q1 * x1.x;
-                acc.y += q0 * x0.y + q1 * x1.y;
-                acc.z += q0 * x0.z + q1 * x1.z;
-                acc.w += q0 * x0.w + q1 * x1.w;
+            for (int j = 0; j < cnt; j += 8) {
+                float4 xx[4];
+                float qq[4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int e = j + sub + 2 * r;
+                    const uint32_t w = __shfl_sync(0xffffffffu, my.x, e & 31);
+                    const float q = __shfl_sync(0xffffffffu, myq, e & 31);
+                    qq[r] = e < cnt ? q : 0.0f;
+                    xx[r] = *reinterpret_cast<const float4 *>(da + (size_t)(e < cnt ? w : 0u) * H + f4);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    acc.x += qq[r] * xx[r].x;
+                    acc.y += qq[r] * xx[r].y;
+                    acc.z += qq[r] * xx[r].z;
+                    acc.w += qq[r] * xx[r].w;
+                }
             }
         }
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
