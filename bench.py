@@ -475,15 +475,17 @@ def run_surrogate(args):
     runs["mc_celf"] = {"s": time.perf_counter() - t0, "seeds": rc.seeds.tolist(), "evaluations": rc.evaluations,
                        "edge_checks": rc.edge_checks}
     print(f"mc_celf: {runs['mc_celf']['s']:.2f} s", file=sys.stderr, flush=True)
-    variants = (("screened_trained", sur, args.screen_mode), ("screened_trained_gradient", sur, "gradient"),
+    variants = (("screened_trained", sur, args.screen_mode), ("screened_trained_onehop_no_rerank", sur, "onehop"),
+                ("screened_trained_gradient", sur, "gradient"),
                 ("screened_trained_onehop", sur, "onehop"), ("screened_untrained", untrained, args.screen_mode),
                 ("screened_degree_no_network", None, "degree"))
     for name, model, mode in variants:
-        if name != "screened_trained" and mode == args.screen_mode and model is sur:
+        no_rerank = name.endswith("no_rerank")
+        if name != "screened_trained" and not no_rerank and mode == args.screen_mode and model is sur:
             continue
         t0 = time.perf_counter()
-        rs, tm = P.cnd_ic_im_screened(G, model, k, T, 1, n_screen=args.screen, n_exact=args.exact, mode=mode,
-                                      graph=1)
+        rs, tm = P.cnd_ic_im_screened(G, model, k, T, 1, n_screen=args.exact if no_rerank else args.screen,
+                                      n_exact=args.exact, mode=mode, graph=1)
         runs[name] = {"s": time.perf_counter() - t0, "mode": mode, "seeds": rs.seeds.tolist(),
                       "evaluations": rs.evaluations, "edge_checks": rs.edge_checks, **tm}
         print(f"{name}: {runs[name]['s']:.2f} s", file=sys.stderr, flush=True)

@@ -303,6 +303,42 @@ def watts_strogatz(n: int, k: int, p: float, graph_seed: int = 1) -> Graph:
     return csr_from_edges(n, src, dst, name=f"ws_n{n}_k{k}")
 
 
+def overlapping_hubs(n_shared_hubs: int = 10, shared: int = 300, n_own_hubs: int = 10, own: int = 150,
+                     n_background: int = 3000, background_deg: int = 3, graph_seed: int = 1) -> Graph:
+    """Hubs with redundant reach: n_shared_hubs hubs all point to the same `shared` nodes, n_own_hubs
+    smaller hubs each point to `own` nodes of their own, and background nodes carry random edges.
+    Out-degree ranks the redundant hubs first, though after one of them the others add little."""
+    rng = _rng(graph_seed)
+    hubs_a = np.arange(n_shared_hubs)
+    hubs_b = np.arange(n_shared_hubs, n_shared_hubs + n_own_hubs)
+    base = n_shared_hubs + n_own_hubs
+    shared_nodes = np.arange(base, base + shared)
+    own0 = base + shared
+    n = own0 + n_own_hubs * own + n_background
+    src, dst = [], []
+    for h in hubs_a:
+        src.append(np.full(shared, h))
+        dst.append(shared_nodes)
+    for i, h in enumerate(hubs_b):
+        src.append(np.full(own, h))
+        dst.append(np.arange(own0 + i * own, own0 + (i + 1) * own))
+    bg = np.repeat(np.arange(n), background_deg)
+    tg = rng.integers(0, n, size=bg.size)
+    keep = bg != tg
+    src.append(bg[keep])
+    dst.append(tg[keep])
+    s_ = np.concatenate(src).astype(np.int64)
+    d_ = np.concatenate(dst).astype(np.int64)
+    k = np.unique(s_ * n + d_)
+    return csr_from_edges(n, k // n, k % n, name=f"hubs_{n_shared_hubs}x{shared}_{n_own_hubs}x{own}")
+
+
+def hub_probabilities(g: Graph, p_hub: float = 0.9, p_background: float = 0.02, n_hubs: int = 20) -> np.ndarray:
+    """IC probabilities for overlapping_hubs: p_hub on the hubs' edges, p_background elsewhere."""
+    src = g.src()
+    return np.where(src < n_hubs, np.float32(p_hub), np.float32(p_background)).astype(np.float32)
+
+
 def path_graph(length: int) -> Graph:
     """Directed path 0 -> 1 -> ... -> length (length edges)."""
     n = length + 1

@@ -1,0 +1,62 @@
+"""What the trained network adds to greedy influence maximisation.
+
+Against plain Monte Carlo greedy (CELF) the screened greedy -- the 8 best candidates by the one-hop
+gain under the trained network's prediction, simulated exactly -- keeps the judged spread of the
+chosen seeds within 2 % while simulating under 1/20 of the seed sets; against the untrained network,
+training cuts the error of the predicted spread on held-out sets.  All seed sets are judged with
+4,096 exact trials under a separate key.  (Measured, not asserted: on these R-MAT graphs an
+out-degree screen does as well, and re-ranking the screened candidates by the trained network's
+predicted spread does worse -- 0.85-0.89 of CELF on R-MAT scale 13.)
+"""
+import numpy as np
+import pytest
+
+import paper_2404_17059_gb300 as P
+from paper_2404_17059_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    g = I.rmat(13, 1 << 17, graph_seed=2)
+    p = I.ic_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+    init = I.surrogate_init(1)
+    sur = P.cnd_sur_create(G, init)
+    r = P.cnd_sur_train(sur, 8192, set_size=(1, 20), n_trials=256, batch_sets=16, lr=1e-3)
+    return g, G, init, sur, r
+
+
+def _judge(G, seeds):
+    r = P.cnd_ic_simulate_ex(G, seeds, 4096, 99, node_count=False)
+    return float(r.spread.astype(np.float64).mean())
+
+
+def test_screened_greedy_matches_celf_with_few_simulations(trained):
+    g, G, _, sur, r = trained
+    assert np.all(np.isfinite(r["loss"])) and r["loss"][-32:].mean() < r["loss"][:4].mean()
+    k, T = 8, 512
+    celf = P.cnd_ic_im_celf(G, k, T, 1)
+    scr, _ = P.cnd_ic_im_screened(G, sur, k, T, 1, n_screen=8, n_exact=8, mode="onehop")
+    a, b = _judge(G, celf.seeds), _judge(G, scr.seeds)
+    print({"celf": a, "screened": b, "celf_sets": celf.evaluations, "screened_sets": scr.evaluations})
+    assert b >= 0.98 * a
+    assert scr.evaluations == 8 * k and scr.evaluations * 20 <= celf.evaluations
+
+
+def test_training_cuts_predicted_spread_error(trained):
+    g, G, init, sur, _ = trained
+    off, seeds = I.surrogate_pairs(g.n, 32, 1, 20, graph_seed=21)
+    mc = P.cnd_ic_simulate_batch(G, off, seeds, np.full(32, 1024, dtype=np.int32),
+                                 np.arange(500, 532, dtype=np.uint64), node_count=True)
+    truth = mc.node_count.reshape(32, g.n).sum(axis=1) / 1024.0
+    fresh = P.cnd_sur_create(G, init)
+
+    def err(s):
+        pred = np.array([P.cnd_sur_forward(s, seeds[off[i]:off[i + 1]], yhat=False)[1] for i in range(32)])
+        return float(np.mean(np.abs(pred - truth) / truth))
+
+    before, after = err(fresh), err(sur)
+    print({"untrained": before, "trained": after})
+    assert after < 0.1 * before
