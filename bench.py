@@ -24,6 +24,10 @@ ingest happens once, before the timed region):
                     surrogate as a screen is timed against MC CELF (1,024
                     common trials); both seed sets are judged with 10,000
                     exact trials.  metric: CELF time / screened-greedy time.
+  surrogate24       surrogate inference over the large graph: R-MAT scale 24 (edge factor 16),
+                    IC p = 0.01, one forward pass per candidate seed set for 1,000 sets of
+                    100 distinct uniform nodes (--items sets); metric: sets/s, with the
+                    forward's algorithmic bytes against the HBM peak.
   celf_rr7          influence maximisation: CELF with k=10 on a random 7-regular
                     graph, n=5,000 (35,000 directed edges), IC with trivalency and
                     weighted-cascade probabilities, 1,000 common trials per
@@ -516,6 +520,44 @@ def run_surrogate(args):
     return 0
 
 
+def run_surrogate24(args):
+    """Surrogate forward passes over R-MAT-24 (n = 16.8 M nodes, 263 M edges)."""
+    import torch
+    import paper_2404_17059_gb300 as P
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    n_sets = args.items or 1000
+    g = I.rmat(24, 16 << 24, graph_seed=1)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, I.ic_uniform(g, 0.01), None)
+    sur = P.cnd_sur_create(G, I.surrogate_init(1))
+    off, seeds = I.surrogate_pairs(g.n, n_sets, 100, 100, graph_seed=24)
+    for i in range(3):
+        P.cnd_sur_forward(sur, seeds[off[i]:off[i + 1]], yhat=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    spreads = [P.cnd_sur_forward(sur, seeds[off[i]:off[i + 1]], yhat=False)[1] for i in range(n_sets)]
+    dt = time.perf_counter() - t0
+    per = dt / n_sets
+    fwd_bytes = 2 * g.m * (128 + 8) + 2 * g.n * 128 + g.n * (64 + 128) + 2 * g.n * (256 + 128)
+    peak, kind = measured_peak()
+    line = {"metric": "surrogate inference: seed sets scored per second", "value": n_sets / dt, "unit": "sets/s",
+            "n_gpus": 1, "steps": n_sets, "warmup": 3, "ms_per_step": per * 1e3, "higher_is_better": True,
+            "scaling": "replicas only", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": f"R-MAT scale 24 edge factor 16 ({g.m} directed edges), IC p=0.01; one "
+                                   f"surrogate forward per seed set of 100 distinct uniform nodes, {n_sets} sets",
+                       "name": "surrogate24", "timing": "host wall clock of each cnd_sur_forward (seed upload, "
+                                                         "all kernels and the spread copy)"},
+            "roofline": {"bound": "hbm", "achieved": fwd_bytes / per / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": fwd_bytes / per / 1e9 / peak, "traffic": None,
+                         "alg_bytes_per_forward": fwd_bytes,
+                         "peak_source": f"{kind} (MEASURED_PEAKS.json hbm_gbs)" if kind == "measured" else "fallback"},
+            "predicted_spread_mean": float(np.mean(spreads))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ----------------------------------------------------------------------------- our arm
 KERNEL = {"ic": "k_push<0>", "lt": "k_push<1>"}
 
@@ -699,7 +741,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ba100k",
-                    choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7", "surrogate"])
+                    choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7", "surrogate", "surrogate24"])
     ap.add_argument("--models", default="ic,lt", help="single-seed-set workloads: models to run (ic, lt or both)")
     ap.add_argument("--pairs", type=int, default=200_000, help="surrogate: training pairs")
     ap.add_argument("--k", type=int, default=50, help="surrogate: seeds to choose")
@@ -723,6 +765,8 @@ def main():
         return run_celf(args)
     if args.workload == "surrogate":
         return run_surrogate(args)
+    if args.workload == "surrogate24":
+        return run_surrogate24(args)
     return run_ours(args)
 
 
