@@ -1,7 +1,7 @@
 // Bit-parallel, level-synchronous Monte Carlo engine for the IC and LT models
 // on sm_103a.
 //
-// Layout.  Trials are packed 64 to a uint64 word; a pass holds B <= 256
+// Layout.  Trials are packed 64 to a uint64 word; a pass holds B <= 2048
 // consecutive words (64*B trials) and every node owns B contiguous words of
 // each state array (node-major), so the state of one node in all of the pass's
 // trials is one contiguous run of 8*B bytes:
@@ -335,40 +335,55 @@ __global__ void __launch_bounds__(kBlock, MODE == 2 ? 4 : 6) k_finalize(Params p
                     const int r = r0 + lane;
                     uint64_t nb = 0;
                     const int w = word_at(dmine[h], dinc[h], min(r, K - 1));
-                    if (r < K) {
-                        const size_t idx = (size_t)v * B + w;
-                        const uint64_t x = p.nxt[idx];
-                        if (MODE == 1) {
-                            nb = x;
-                        } else {
-                            uint64_t *cw = p.cvt + (size_t)v * nq + (w >> 6);
-                            if ((*cw >> (w & 63)) & 1ull) {
-                                nb = x;
-                            } else {
+                    const size_t idx = (size_t)v * B + w;
+                    if (MODE == 1) {
+                        if (r < K) nb = p.nxt[idx];
+                    } else {
+                        // LT: a row converted earlier in this pass carries the activations its push
+                        // detected; a row touched for the first time is converted here by a
+                        // half-warp (one lane per 4-trial block, coalesced 256-byte row)
+                        uint64_t *cw = p.cvt + (size_t)v * nq + (w >> 6);
+                        const bool conv = r < K && ((*cw >> (w & 63)) & 1ull);
+                        const uint64_t x = r < K ? p.nxt[idx] : 0ull;
+                        if (conv) nb = x;
+                        unsigned need = __ballot_sync(kFull, r < K && !conv);
+                        const int hl = lane & 15;
+                        while (need) {
+                            const int l0 = __ffs(need) - 1;
+                            need &= need - 1;
+                            const int l1 = need ? __ffs(need) - 1 : -1;
+                            if (need) need &= need - 1;
+                            const int own = lane < 16 ? l0 : (l1 >= 0 ? l1 : l0);
+                            const bool act = lane < 16 || l1 >= 0;
+                            const int ow = __shfl_sync(kFull, w, own);
+                            const size_t oidx = (size_t)v * B + ow;
+                            uint64_t bits = 0;
+                            if (act) {
+                                ++n_dr;
+                                const U4 th = draw<PERWORD>(p, ow, (uint32_t)v, word_g0<PERWORD>(p, ow) + (uint64_t)hl, 1u);
+                                uint4 *a4 = reinterpret_cast<uint4 *>(p.acc + oidx * 64) + hl;
+                                uint4 s4 = *a4;
+                                bits = ((uint64_t)(s4.x > th.x) | ((uint64_t)(s4.y > th.y) << 1) |
+                                        ((uint64_t)(s4.z > th.z) << 2) | ((uint64_t)(s4.w > th.w) << 3))
+                                       << (4 * hl);
+                                s4.x += ~th.x;
+                                s4.y += ~th.y;
+                                s4.z += ~th.z;
+                                s4.w += ~th.w;
+                                *a4 = s4;
+                            }
+                            // or the 16 lanes' 4-bit pieces within each half-warp
+#pragma unroll
+                            for (int o = 1; o < 16; o <<= 1) bits |= __shfl_xor_sync(kFull, bits, o);
+                            const uint64_t b0 = __shfl_sync(kFull, bits, 0), b1 = __shfl_sync(kFull, bits, 16);
+                            if (lane == l0 || lane == l1) {
                                 const uint64_t vis = p.vis[idx];
-                                uint4 *a4 = reinterpret_cast<uint4 *>(p.acc + idx * 64);
-                                const uint64_t g0 = word_g0<PERWORD>(p, w);
-#pragma unroll 2
-                                for (int j = 0; j < 16; ++j) {
-                                    ++n_dr;
-                                    const U4 th = draw<PERWORD>(p, w, (uint32_t)v, g0 + (uint64_t)j, 1u);
-                                    uint4 s4 = a4[j];
-                                    const uint64_t hit = (uint64_t)(s4.x > th.x) | ((uint64_t)(s4.y > th.y) << 1) |
-                                                         ((uint64_t)(s4.z > th.z) << 2) |
-                                                         ((uint64_t)(s4.w > th.w) << 3);
-                                    nb |= hit << (4 * j);
-                                    s4.x += ~th.x;
-                                    s4.y += ~th.y;
-                                    s4.z += ~th.z;
-                                    s4.w += ~th.w;
-                                    a4[j] = s4;
-                                }
-                                nb &= ~vis;
+                                nb = (lane == l0 ? b0 : b1) & ~vis;
                                 if (nb) p.vis[idx] = vis | nb;
                                 atomicOr((unsigned long long *)cw, 1ull << (w & 63));
                             }
-                            p.nxt[idx] = nb;
                         }
+                        if (r < K) p.nxt[idx] = nb;
                     }
                     bool wait = nb != 0ull && __popcll(nb) < tau;
                     if (nb != 0ull && tau > 0 && p.max_wait > 0) {
