@@ -48,6 +48,38 @@ def test_im_opts_layout_and_host_validation():
     assert "required" in P.cnd_last_error()
 
 
+def test_surrogate_and_screen_abi_on_host():
+    """Struct layouts, defaults, and NULL-handle rejection of the surrogate and screened-greedy entry points
+    (all checked on the host, before any CUDA call)."""
+    import ctypes
+    L = binding.load()
+    assert ctypes.sizeof(binding.cnd_sur_train_opts) == 112
+    assert ctypes.sizeof(binding.cnd_screen_opts) == 56
+    assert binding.cnd_screen_opts.sur_ms_out.offset == 16
+    o = binding.cnd_sur_train_opts()
+    L.cnd_sur_train_opts_init(ctypes.byref(o))
+    assert (o.set_size_lo, o.set_size_hi, o.n_trials, o.batch_sets, o.sim_chunk) == (1, 50, 1024, 16, 256)
+    assert abs(o.lr - 1e-3) < 1e-9 and o.n_pairs == 0
+    buf = np.zeros(binding.CND_SUR_N_PARAMS, dtype=np.float32)
+    out = ctypes.c_void_p()
+    assert L.cnd_sur_create(None, buf.ctypes.data, ctypes.byref(out)) == P.CND_EINVAL and not out.value
+    for name, args in (("cnd_sur_set_params", (None, buf.ctypes.data)), ("cnd_sur_get_params", (None, buf.ctypes.data)),
+                       ("cnd_sur_forward", (None, None, 0, None, None)),
+                       ("cnd_sur_loss_grad", (None, None, 0, buf.ctypes.data, None, None)),
+                       ("cnd_sur_adam", (None, buf.ctypes.data, ctypes.c_float(1e-3))),
+                       ("cnd_sur_scores", (None, None, 0, buf.ctypes.data)),
+                       ("cnd_sur_onehop", (None, None, 0, buf.ctypes.data)),
+                       ("cnd_sur_train", (None, ctypes.byref(o), None))):
+        assert getattr(L, name)(*args) == P.CND_EINVAL, name
+        assert "NULL" in P.cnd_last_error() or "required" in P.cnd_last_error(), name
+    L.cnd_sur_destroy(None)  # NULL-safe
+    io = binding.cnd_im_opts()
+    L.cnd_im_opts_init(ctypes.byref(io))
+    so = binding.cnd_screen_opts()
+    seeds = np.zeros(4, dtype=np.int32)
+    assert L.cnd_ic_im_screened(None, None, ctypes.byref(io), ctypes.byref(so), seeds.ctypes.data, None) == P.CND_EINVAL
+
+
 def _graph():
     return I.erdos_renyi_m(50, 200, graph_seed=2)
 
