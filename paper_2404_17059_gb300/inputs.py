@@ -115,6 +115,16 @@ def erdos_renyi_m(n: int, m: int, graph_seed: int = 1) -> Graph:
     return csr_from_edges(n, chosen // n, chosen % n, name=f"er_n{n}_m{m}")
 
 
+def erdos_renyi_gnp(n: int, p: float, graph_seed: int = 1) -> Graph:
+    """Undirected G(n, p) (every pair independently with probability p), both directions stored."""
+    rng = _rng(graph_seed)
+    iu, ju = np.triu_indices(n, k=1)
+    keep = rng.random(iu.size) < p
+    u = iu[keep].astype(np.int64)
+    v = ju[keep].astype(np.int64)
+    return csr_from_edges(n, np.concatenate([u, v]), np.concatenate([v, u]), name=f"gnp_n{n}_p{p}")
+
+
 def barabasi_albert(n: int, m_attach: int, graph_seed: int = 1) -> Graph:
     """Barabasi-Albert preferential attachment, each undirected edge stored both ways.
 
