@@ -102,3 +102,18 @@ def test_screened_greedy_degree_mode_needs_no_network(er0):
     deg = np.diff(g.row_ptr)
     assert r.seeds[0] in np.argsort(-deg, kind="stable")[:2]
     assert r.evaluations == 3 * 2 and tm["sur_ms"] >= 0
+
+
+def test_celf_takes_every_candidate_and_isolated_nodes(er0):
+    g, G, p, _ = er0
+    cand = np.array([5, 17, 42, 99, 600], dtype=np.int32)
+    r = P.cnd_ic_im_celf(G, len(cand), 64, 9, candidates=cand)
+    s, f, _ = im.celf("ic", g, len(cand), 64, 9, candidates=cand, ic_prob=p)
+    np.testing.assert_array_equal(r.seeds, s)
+    np.testing.assert_array_equal(r.f, f)
+    assert sorted(r.seeds.tolist()) == sorted(cand.tolist())
+    # isolated nodes: every candidate spreads to itself only; ties go to the lowest id
+    h = I.csr_from_edges(6, np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.int64))
+    H = P.cnd_graph_create(h.n, h.row_ptr, h.col, np.zeros(0, dtype=np.float32), None)
+    r = P.cnd_ic_im_celf(H, 3, 32, 1)
+    assert r.seeds.tolist() == [0, 1, 2] and r.f.tolist() == [32, 64, 96]

@@ -141,3 +141,40 @@ def test_onehop_scores_match_oracle(setup):
     sc = P.cnd_sur_onehop(sur, seeds)
     ref, _ = S.onehop_scores(params.astype(np.float64), OG, seeds)
     np.testing.assert_allclose(sc, ref, rtol=1e-2, atol=1e-2)
+
+
+def test_degenerate_graphs_match_oracle():
+    """Edgeless graph, a single node, and every node a seed."""
+    params = I.surrogate_init(5) * 2.0
+    for n, src, dst in ((50, [], []), (1, [], []), (40, list(range(39)), list(range(1, 40)))):
+        g = I.csr_from_edges(n, np.asarray(src, dtype=np.int64), np.asarray(dst, dtype=np.int64))
+        p = np.full(g.m, 0.5, dtype=np.float32)
+        G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+        sur = P.cnd_sur_create(G, params)
+        OG = S.Graph(g, p)
+        for seeds in ([], [0], list(range(n))):
+            yh, tot = P.cnd_sur_forward(sur, seeds)
+            ref = S.forward(params.astype(np.float32).astype(np.float64), OG, seeds)["yhat"]
+            np.testing.assert_allclose(yh, ref, rtol=0, atol=5e-3)
+            if len(seeds) == n:
+                assert np.all(yh == 1.0) and abs(tot - n) < 1e-9
+            y = np.zeros(n, dtype=np.float32)
+            loss, grad = P.cnd_sur_loss_grad(sur, seeds, y)
+            rl, rg, _ = S.loss_and_grad(params.astype(np.float32).astype(np.float64), OG, seeds, y.astype(np.float64))
+            assert abs(loss - rl) <= 1e-3 * max(rl, 1e-12) + 1e-12
+            assert np.abs(grad - rg).max() <= 0.02 * max(np.abs(rg).max(), 1e-12) + 1e-7
+
+
+def test_bad_arguments_are_rejected(setup):
+    g, OG, G, sur, params = setup
+    with pytest.raises(P.CndError):
+        P.cnd_sur_forward(sur, [g.n])
+    with pytest.raises(P.CndError):
+        P.cnd_sur_forward(sur, [-1])
+    bad = params.copy()
+    bad[7] = np.nan
+    with pytest.raises(P.CndError):
+        P.cnd_sur_set_params(sur, bad)
+    G2 = P.cnd_graph_create(g.n, g.row_ptr, g.col, None, I.lt_weighted_cascade(g))
+    with pytest.raises(P.CndError):
+        P.cnd_sur_create(G2, params)  # no IC probabilities
