@@ -130,7 +130,9 @@ typedef struct cnd_sim_opts {
                                   least fixed point do not depend on the order of expansion), but
                                   steps no longer are activation times, so level counts and
                                   max_levels are refused (CND_EINVAL); 0 = off, at most 64 */
-    double timeout_s;          /* > 0: give up with CND_ETIMEOUT after this many seconds */
+    double timeout_s;          /* > 0: give up with CND_ETIMEOUT after this many seconds (checked
+                                  between steps: by the host, or in a CUDA-graph call by the
+                                  step-control kernel on the GPU's global timer) */
     cnd_sim_stats *stats;      /* NULL or host struct filled by the call */
     int32_t defer_steps;       /* with defer_bits: a word waits at most this many steps (0 = until
                                   nothing else is left to expand) */

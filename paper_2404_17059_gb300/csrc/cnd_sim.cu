@@ -78,9 +78,16 @@ struct Ctl {
     int32_t force;   // 1: every waiting word is expanded now
     int32_t pull;    // 1: this step pulls (IC)
     int32_t limit;   // a pass stopped at max_levels with trials still active
-    int32_t pad;
+    int32_t timed_out;  // the device loop stopped at its time limit
     unsigned long long slots, items, levels, pull_steps;
+    unsigned long long t0;  // global timer (ns) when the call's first step began
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 struct Params {
     int32_t n, B, nq;
@@ -855,9 +862,15 @@ __global__ void k_pass_begin(Params p) {
 // The host loop's decision, on the device: run step L (the first step of a
 // pass, or the one after the step just finalized)?  Prepares its counters and
 // sets the WHILE condition of the pass's step loop.
+// The device loop's step control (one thread): census of the frontier the last step produced,
+// stop at an empty frontier, the level cap or the time limit (timeout_ns > 0, measured on the GPU's
+// global timer from the call's first step), else set up the next step.
 __global__ void k_ctl(Params p, cudaGraphConditionalHandle h, int32_t first, int32_t max_levels, int32_t may_pull,
-                      int32_t pull_always, int32_t permille, int64_t m, int32_t tau) {
+                      int32_t pull_always, int32_t permille, int64_t m, int32_t tau,
+                      unsigned long long timeout_ns) {
     Ctl *c = p.ctl;
+    const unsigned long long now = global_ns();
+    if (c->t0 == 0ull) c->t0 = now;
     const int L = first ? 0 : c->level + 1;
     const bool odd = (L & 1) != 0;
     const int32_t *cnt = odd ? p.fr[1].cnt : p.fr[0].cnt;
@@ -866,7 +879,10 @@ __global__ void k_ctl(Params p, cudaGraphConditionalHandle h, int32_t first, int
     c->slots += (unsigned long long)slots;
     c->items += (unsigned long long)items;
     int go = 1;
-    if (slots == 0 && waiting == 0) {
+    if (c->timed_out || (timeout_ns > 0ull && now - c->t0 > timeout_ns)) {
+        c->timed_out = 1;
+        go = 0;
+    } else if (slots == 0 && waiting == 0) {
         go = 0;
     } else if (max_levels > 0 && L >= max_levels) {
         c->limit = 1;
@@ -1415,6 +1431,8 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
             return cudaStreamEndCapture(cs, &gout);
         };
         const int body_kernels = (may_pull ? 3 : 0) + 3;
+        const unsigned long long timeout_ns =
+            o.timeout_s > 0 ? (unsigned long long)std::max(1.0, std::min(o.timeout_s * 1e9, 1.8e19)) : 0ull;
         for (size_t pass = 0; pass < passes.size(); ++pass) {
             const std::vector<Seg> &ps = passes[pass];
             Params Q = pass_params(pass, P);
@@ -1437,7 +1455,7 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
                                                                       seeds_dev, d_bad);
             CND_CUDA_TRY(launch(k_seedfin, seed_blocks, cs, Q));
             k_ctl<<<1, 1, 0, cs>>>(Q, h, 1, o.max_levels, may_pull ? 1 : 0, o.direction == CND_DIR_PULL ? 1 : 0,
-                                   permille, (int64_t)G.m, P.tau);
+                                   permille, (int64_t)G.m, P.tau, timeout_ns);
             CND_CUDA_TRY(cudaGetLastError());
             CND_CUDA_TRY(cap_end(&tail));
             // the step loop
@@ -1458,7 +1476,7 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
             CND_CUDA_TRY(launch(pw ? k_push_pw : k_push_uk, push_blocks, cs, Q));
             CND_CUDA_TRY(launch(pw ? k_fin_pw : k_fin_uk, fin_blocks, cs, Q));
             k_ctl<<<1, 1, 0, cs>>>(Q, h, 0, o.max_levels, may_pull ? 1 : 0, o.direction == CND_DIR_PULL ? 1 : 0,
-                                   permille, (int64_t)G.m, P.tau);
+                                   permille, (int64_t)G.m, P.tau, timeout_ns);
             CND_CUDA_TRY(cudaGetLastError());
             CND_CUDA_TRY(cap_end(nullptr));
             tail.assign(1, loop_node);
@@ -1479,6 +1497,10 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
         Ctl hc;
         CND_CUDA_TRY(cudaMemcpyAsync(&hc, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CND_CUDA_TRY(cudaStreamSynchronize(st));
+        if (hc.timed_out) {
+            set_error("%s: timed out after %.3f s (device loop)", fn, o.timeout_s);
+            return CND_ETIMEOUT;
+        }
         if (hc.limit) limit_hit = true;
         launches += (int64_t)hc.levels * body_kernels;
         if (S) {

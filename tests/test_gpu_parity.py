@@ -397,3 +397,16 @@ def test_autotune_keeps_results(ba, rmat14):
     want_sp, want_nc, want_ck = _batch_ref("lt", g, p, w, seed_off, seeds2, trials, keys)
     a = P.cnd_lt_simulate_batch(G, seed_off, seeds2, trials, keys, edge_checks=True, autotune=1)
     assert np.array_equal(a.spread, want_sp) and a.edge_checks == want_ck
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+def test_timeout_stops_the_call_and_leaves_the_context_usable(ba, graph):
+    """Failure detection without a fault: a time limit far below the call's run time ends it with
+    CND_ETIMEOUT (host watchdog per step, or the device loop's check of the GPU global timer), and
+    the next call on the same graph still gives the oracle's results."""
+    g, G, p, w, seeds = ba
+    with pytest.raises(P.CndError) as ei:
+        sim("lt", G, seeds, 10_000, 1, timeout_s=1e-4, graph=graph)
+    assert ei.value.status == P.CND_ETIMEOUT
+    assert "timed out" in P.cnd_last_error()
+    assert_same(sim("lt", G, seeds, 640, 1, graph=graph), ref("lt", g, seeds, 640, 1, w=w))
