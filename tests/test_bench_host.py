@@ -1,0 +1,63 @@
+"""Host logic of bench.py: the algorithmic-byte count of the expansion kernels, the traffic lookup keyed
+by the engine sources, model selection and the derived integer-multiply peak (no GPU needed)."""
+import json
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_alg_bytes_per_term():
+    base = {"work_items": 1, "frontier_words": 0, "edges_scanned": 0, "word_checks": 0, "updates": 0}
+    assert bench.alg_bytes("ic", base) == 8
+    for key in ("frontier_words", "edges_scanned", "word_checks"):
+        s = dict(base, work_items=0, **{key: 1})
+        assert bench.alg_bytes("ic", s) == 8 and bench.alg_bytes("lt", s) == 8
+    s = dict(base, work_items=0, updates=1)
+    assert bench.alg_bytes("ic", s) == 16   # vis and nxt read-modify-write
+    assert bench.alg_bytes("lt", s) == 8    # one 4-byte accumulator read and write
+
+
+def test_philox_peak_from_unit_counts():
+    # 152 SMs x 64 multiplies per clock x 2.07 GHz, 40 multiply results per Philox-4x32-10 call
+    assert bench.PHILOX_PEAK_G == pytest.approx(152 * 64 * 2.07 / 40)
+    assert 500 < bench.PHILOX_PEAK_G < 510
+
+
+def test_traffic_lookup_needs_the_current_sources(tmp_path, monkeypatch):
+    cur = bench.source_hash()
+    assert len(cur) == 12
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    lines = ["# comment", json.dumps({"kernel": "k_push<1>", "workload": "ba100k", "src": cur,
+                                      "dram_bytes_per_word_check": 100.0}),
+             json.dumps({"kernel": "k_push<0>", "workload": "ba100k", "src": "000000000000",
+                         "dram_bytes_per_word_check": 10.0})]
+    (prof / "traffic.txt").write_text("\n".join(lines) + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "source_hash", lambda: cur)
+    assert bench.ncu_traffic("k_push<1>", "ba100k", 3.0) == 300.0
+    assert bench.ncu_traffic("k_push<0>", "ba100k", 3.0) is None   # taken on other sources
+    assert bench.ncu_traffic("k_push<1>", "rmat24", 3.0) is None
+
+
+def test_committed_traffic_matches_the_engine():
+    """The committed traffic figures were taken on the current engine sources."""
+    assert bench.ncu_traffic("k_push<1>", "ba100k", 1.0) is not None
+    assert bench.ncu_traffic("k_push<0>", "ba100k", 1.0) is not None
+    assert bench.ncu_traffic("k_push<0>", "rmat24", 1.0) is not None
+
+
+def test_select_models():
+    wl = bench.make_workload("er1k")
+    assert set(m for m, d in wl.models.items() if d is not None) == {"ic", "lt"}
+    wl = bench.select_models(bench.make_workload("er1k"), "lt")
+    assert wl.models["ic"] is None and wl.models["lt"] is not None
+    assert wl.trials_per_step() == 1000
+    with pytest.raises(SystemExit):
+        bench.select_models(bench.make_workload("er1k"), "xx")
