@@ -24,10 +24,12 @@ ingest happens once, before the timed region):
                     surrogate as a screen is timed against MC CELF (1,024
                     common trials); both seed sets are judged with 10,000
                     exact trials.  metric: CELF time / screened-greedy time.
-  surrogate24       surrogate inference over the large graph: R-MAT scale 24 (edge factor 16),
-                    IC p = 0.01, one forward pass per candidate seed set for 1,000 sets of
-                    100 distinct uniform nodes (--items sets); metric: sets/s, with the
-                    forward's algorithmic bytes against the HBM peak.
+  surrogate24       surrogate inference over the large graph: R-MAT scale 24 (edge factor 16,
+                    --scale to change), IC p = 0.01, one forward pass per candidate seed set
+                    for 1,000 sets of 100 distinct uniform nodes (--items sets); metric:
+                    sets/s, with the forward's algorithmic bytes against the HBM peak.
+  rmat20batch_full  all 4,096 seed sets of the batched workload in one call (one CUDA graph),
+                    after one warm-up call on 8 of them; about 150 s on one GB300.
   table1            the paper's run-time table scenario: IC, 1,000 runs from 100 uniform seeds on
                     an undirected G(n=2000, p=0.002) and a Watts-Strogatz (n=10000, k=10,
                     p=0.007) graph (edges both ways), trivalency / uniform [0,1] / weighted-
@@ -576,6 +578,37 @@ def run_table1(args):
     return 0
 
 
+def run_batch_full(args):
+    """The whole batched workload (4,096 seed sets, 7.3 M trials) in one call."""
+    import torch
+    import paper_2404_17059_gb300 as P
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return 0
+    g = I.rmat(20, 1 << 24, graph_seed=1)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, I.ic_uniform_random(g, 0.1, graph_seed=1), None)
+    so, seeds, tr, keys = I.batch_items(g.n, 4096, 1, 100, (256, 1024, 4096), graph_seed=1)
+    sd = torch.as_tensor(seeds, device="cuda")
+    P.cnd_ic_simulate_batch(G, so[:9], sd[:so[8]], tr[:8], keys[:8], graph=1, edge_checks=True)  # first-use costs
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = P.cnd_ic_simulate_batch(G, so, sd, tr, keys, graph=1, edge_checks=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": r.edge_checks / dt, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic",
+            "config": {"workload": f"R-MAT scale 20 ({g.m} directed edges), IC p~U[0,0.1) fp32 per edge; all 4096 "
+                                   "seed sets (|S|~U{1..100}, trials from {256,1024,4096}, rng_seed i+1) in one call",
+                       "name": "rmat20batch_full", "timing": "host wall clock around the call (one CUDA graph)"},
+            "trials_per_s": float(tr.sum()) / dt, "edge_checks": r.edge_checks, "trials": int(tr.sum()),
+            "words": int(((tr.astype(np.int64) + 63) // 64).sum()),
+            "mean_spread": float(r.spread.to(torch.float64).mean().item())}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_surrogate24(args):
     """Surrogate forward passes over R-MAT-24 (n = 16.8 M nodes, 263 M edges)."""
     import torch
@@ -585,7 +618,7 @@ def run_surrogate24(args):
     if rank != 0:
         return 0
     n_sets = args.items or 1000
-    g = I.rmat(24, 16 << 24, graph_seed=1)
+    g = I.rmat(args.scale, 16 << args.scale, graph_seed=1)
     G = P.cnd_graph_create(g.n, g.row_ptr, g.col, I.ic_uniform(g, 0.01), None)
     sur = P.cnd_sur_create(G, I.surrogate_init(1))
     off, seeds = I.surrogate_pairs(g.n, n_sets, 100, 100, graph_seed=24)
@@ -601,7 +634,7 @@ def run_surrogate24(args):
     line = {"metric": "surrogate inference: seed sets scored per second", "value": n_sets / dt, "unit": "sets/s",
             "n_gpus": 1, "steps": n_sets, "warmup": 3, "ms_per_step": per * 1e3, "higher_is_better": True,
             "scaling": "replicas only", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": f"R-MAT scale 24 edge factor 16 ({g.m} directed edges), IC p=0.01; one "
+            "config": {"workload": f"R-MAT scale {args.scale} edge factor 16 ({g.m} directed edges), IC p=0.01; one "
                                    f"surrogate forward per seed set of 100 distinct uniform nodes, {n_sets} sets",
                        "name": "surrogate24", "timing": "host wall clock of each cnd_sur_forward (seed upload, "
                                                          "all kernels and the spread copy)"},
@@ -798,7 +831,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="ba100k",
                     choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7", "surrogate", "surrogate24",
-                             "table1"])
+                             "table1", "rmat20batch_full"])
+    ap.add_argument("--scale", type=int, default=24, help="surrogate24: R-MAT scale")
     ap.add_argument("--models", default="ic,lt", help="single-seed-set workloads: models to run (ic, lt or both)")
     ap.add_argument("--pairs", type=int, default=200_000, help="surrogate: training pairs")
     ap.add_argument("--k", type=int, default=50, help="surrogate: seeds to choose")
@@ -826,6 +860,8 @@ def main():
         return run_surrogate24(args)
     if args.workload == "table1":
         return run_table1(args)
+    if args.workload == "rmat20batch_full":
+        return run_batch_full(args)
     return run_ours(args)
 
 
