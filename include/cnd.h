@@ -72,7 +72,7 @@ typedef int32_t cnd_status;
 #define CND_ENOMEM (-2)    /* device or host allocation failed */
 #define CND_ECUDA (-3)     /* CUDA runtime error (no device, launch failure, ...) */
 #define CND_ELIMIT (-4)    /* some trial still had newly active nodes at step max_levels */
-#define CND_ETIMEOUT (-5)  /* host watchdog expired; outputs are not valid */
+#define CND_ETIMEOUT (-5)  /* time limit (timeout_s) reached; outputs are not valid */
 #define CND_EOVERFLOW (-6) /* LT in-weights of a node sum above 2^32 - 1 */
 
 #define CND_DIR_AUTO 0 /* push or pull per step, by frontier size (see pull_permille) */
@@ -226,8 +226,8 @@ cnd_status cnd_lt_simulate_batch(const cnd_graph *g, int32_t n_items, const int6
  * work (at most 4,096 trials of a single seed set, or the first 4 items of a
  * batch with at most 512 trials each) and writes the fastest into *best_out
  * (a copy of *base with word_bits, chunk_edges, pull_permille and graph set).
- * The candidates: pass widths of 256, 64 and 16 words (single seed sets; the
- * widest for batches); 0 (by frontier words),
+ * The candidates: the widest pass that fits (up to 2,048 words), 64 and 16
+ * words (single seed sets; the widest for batches); 0 (by frontier words),
  * 32 and 512 edges per work item; push only or pull above 25 % of m (IC);
  * host loop or one CUDA graph per call.  The result is cached per (graph,
  * model, single or batch, log2 trials, log2 seeds) for opts.autotune.
