@@ -44,16 +44,20 @@ def test_trial_shard_partitions():
         trial_shard(10, 2, 2)
 
 
-def _run_world2(tmp_path, backend, case):
+def _run_world(tmp_path, backend, case, world=2):
     port = _free_port()
     ctx = mp.get_context("spawn")
-    procs = [ctx.Process(target=W.run, args=(r, 2, port, backend, str(tmp_path), case)) for r in range(2)]
+    procs = [ctx.Process(target=W.run, args=(r, world, port, backend, str(tmp_path), case)) for r in range(world)]
     for p in procs:
         p.start()
     for p in procs:
         p.join(timeout=300)
     assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
-    return [np.load(os.path.join(tmp_path, f"rank{r}.npz"), allow_pickle=True) for r in range(2)]
+    return [np.load(os.path.join(tmp_path, f"rank{r}.npz"), allow_pickle=True) for r in range(world)]
+
+
+def _run_world2(tmp_path, backend, case):
+    return _run_world(tmp_path, backend, case, 2)
 
 
 def _single(case):
@@ -75,6 +79,38 @@ def test_world2_gloo_matches_single_process(tmp_path, case):
         np.testing.assert_array_equal(o["node_count"], ref.node_count)
         assert int(o["edge_checks"]) == ref.edge_checks
         np.testing.assert_array_equal(o["level_counts"], ref.level_counts[:32])
+
+
+def test_world3_uneven_ranges(tmp_path):
+    """Three ranks, a trial count that leaves the last rank a short range."""
+    case = {"model": "ic", "n_trials": 200, "rng_seed": 3}
+    outs = _run_world(tmp_path, "oracle", case, 3)
+    ref = _single(case)
+    assert [int(o["count"]) for o in outs] == [64, 64, 72]
+    for o in outs:
+        np.testing.assert_array_equal(o["spread"], ref.spread)
+        np.testing.assert_array_equal(o["node_count"], ref.node_count)
+        assert int(o["edge_checks"]) == ref.edge_checks
+
+
+def test_trial_shard_properties():
+    hypothesis = pytest.importorskip("hypothesis")
+    st = hypothesis.strategies
+
+    @hypothesis.given(st.integers(0, 10**7), st.integers(1, 64))
+    @hypothesis.settings(max_examples=200, deadline=None)
+    def check(T, world):
+        ranges = [trial_shard(T, r, world) for r in range(world)]
+        assert sum(c for _, c in ranges) == T
+        pos = 0
+        for first, cnt in ranges:
+            if cnt:
+                assert first == pos and first % 64 == 0
+            pos += cnt
+        counts = [c for _, c in ranges]
+        assert max(counts) - min(counts) <= 64
+
+    check()
 
 
 @pytest.mark.gpu
