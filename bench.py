@@ -22,7 +22,7 @@ ingest happens once, before the timed region):
                     sets (|S| ~ U{1..50}, 1,024 exact trials each, generated on
                     the fly by the simulator), then greedy k=50 with the
                     surrogate as a screen is timed against MC CELF (1,024
-                    common trials); both seed sets are judged with 10,000
+                    common trials); both seed sets are scored with 10,000
                     exact trials.  metric: CELF time / screened-greedy time.
   surrogate24       surrogate inference over the large graph: R-MAT scale 24 (edge factor 16,
                     --scale to change), IC p = 0.01, one forward pass per candidate seed set
@@ -430,7 +430,7 @@ def run_surrogate(args):
     torch.cuda.set_device(local)
     if rank != 0:
         return 0
-    k, T, judge_T, judge_key = args.k, 1024, 10_000, 7777
+    k, T, score_T, score_key = args.k, 1024, 10_000, 7777
     g = I.rmat(17, 1 << 21, graph_seed=1)
     p = I.ic_weighted_cascade(g)
     G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
@@ -475,8 +475,8 @@ def run_surrogate(args):
     print(f"trained {args.pairs} pairs in {train_s:.1f} s; held-out before {q0} after {q1}", file=sys.stderr,
           flush=True)
 
-    def judge(seeds):
-        r = P.cnd_ic_simulate_ex(G, seeds, judge_T, judge_key, node_count=False)
+    def mc_spread(seeds):
+        r = P.cnd_ic_simulate_ex(G, seeds, score_T, score_key, node_count=False)
         return float(r.spread.astype(np.float64).mean())
 
     runs = {}
@@ -501,12 +501,12 @@ def run_surrogate(args):
                       "evaluations": rs.evaluations, "edge_checks": rs.edge_checks, **tm}
         print(f"{name}: {runs[name]['s']:.2f} s", file=sys.stderr, flush=True)
     for v in runs.values():
-        v["judged_spread"] = judge(v["seeds"])
+        v["scored_spread"] = mc_spread(v["seeds"])
     base = runs["mc_celf"]
     for name in runs:
         if name == "mc_celf":
             continue
-        runs[name]["spread_vs_celf"] = runs[name]["judged_spread"] / base["judged_spread"]
+        runs[name]["spread_vs_celf"] = runs[name]["scored_spread"] / base["scored_spread"]
         runs[name]["speedup_vs_celf"] = base["s"] / runs[name]["s"]
     line = {"metric": "surrogate vs MC greedy speedup", "value": runs["screened_trained"]["speedup_vs_celf"],
             "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * runs["screened_trained"]["s"],
@@ -516,7 +516,7 @@ def run_surrogate(args):
                                    f"{args.pairs} pairs (|S|~U{{1..50}}, {T} trials); greedy k={k} screened "
                                    f"({args.screen} by the {args.screen_mode} score, then by predicted spread, "
                                    f"{args.exact} simulated per round) vs MC CELF, "
-                                   f"{T} common trials; judged with {judge_T} trials (key {judge_key})",
+                                   f"{T} common trials; scored with {score_T} trials (key {score_key})",
                        "name": "surrogate"},
             "spread_vs_celf": runs["screened_trained"]["spread_vs_celf"],
             "training": {"pairs": args.pairs, "s": train_s, "sim_ms": tr["sim_ms"], "train_ms": tr["train_ms"],

@@ -296,8 +296,8 @@ cnd_status cnd_lt_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *see
 /*
  * Learned surrogate of IC activation frequencies, for screening candidate
  * seeds in greedy influence maximisation (Sec. 2 "Influence Maximization";
- * the paper has no learned component -- the exact simulator above stays the
- * judge).  A 3-layer message-passing network, hidden width 64, maps a seed
+ * the paper has no learned component -- the exact simulator above makes
+ * every decision).  A 3-layer message-passing network, hidden width 64, maps a seed
  * set S to yhat_v, a prediction of the fraction of trials in which node v
  * ends active (the per-node counts of the paper's activation heatmap, Sec. 4,
  * over the trial count):
@@ -395,7 +395,7 @@ cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, double *loss_o
  *      Carlo engine (common random numbers as in CELF: trials first_trial ..
  *      first_trial + n_trials - 1 of key rng_seed) and choose the best
  *      (ties: lower id).
- * The simulator is the judge of every choice; the network only decides which
+ * The simulator makes every choice; the network only decides which
  * candidates it sees.  o->k, n_trials, rng_seed, candidates, max_items, sim,
  * stream, evaluations_out and edge_checks_out as for CELF (eval_batch
  * unused).  seeds_out[j], f_out[j] (may be NULL) as for CELF.

@@ -1,8 +1,8 @@
 """Learned surrogate of the IC activation frequencies -- fp64 CPU oracle, TEST INFRASTRUCTURE ONLY.
 
 The paper has no learned component; this network exists to screen candidate
-seeds in greedy influence maximisation (Sec. 2 "Influence Maximization"), with
-the exact Monte Carlo simulator as the judge.  It maps a seed set S to a
+seeds in greedy influence maximisation (Sec. 2 "Influence Maximization"), while
+the exact Monte Carlo simulator makes every decision.  It maps a seed set S to a
 prediction of every node's activation frequency under IC (the per-node counts
 of the paper's activation heatmap, Sec. 4 "Visualizations", divided by the
 trial count).

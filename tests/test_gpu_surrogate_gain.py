@@ -1,9 +1,9 @@
 """What the trained network adds to greedy influence maximisation.
 
 Against plain Monte Carlo greedy (CELF) the screened greedy -- the 8 best candidates by the one-hop
-gain under the trained network's prediction, simulated exactly -- keeps the judged spread of the
+gain under the trained network's prediction, simulated exactly -- keeps the simulated spread of the
 chosen seeds within 2 % while simulating under 1/20 of the seed sets; against the untrained network,
-training cuts the error of the predicted spread on held-out sets.  All seed sets are judged with
+training cuts the error of the predicted spread on held-out sets.  All seed sets are scored with
 4,096 exact trials under a separate key.  (Measured, not asserted: on these R-MAT graphs an
 out-degree screen does as well, and re-ranking the screened candidates by the trained network's
 predicted spread does worse -- 0.85-0.89 of CELF on R-MAT scale 13.)
@@ -28,7 +28,7 @@ def trained():
     return g, G, init, sur, r
 
 
-def _judge(G, seeds):
+def _mc_spread(G, seeds):
     r = P.cnd_ic_simulate_ex(G, seeds, 4096, 99, node_count=False)
     return float(r.spread.astype(np.float64).mean())
 
@@ -39,7 +39,7 @@ def test_screened_greedy_matches_celf_with_few_simulations(trained):
     k, T = 8, 512
     celf = P.cnd_ic_im_celf(G, k, T, 1)
     scr, _ = P.cnd_ic_im_screened(G, sur, k, T, 1, n_screen=8, n_exact=8, mode="onehop")
-    a, b = _judge(G, celf.seeds), _judge(G, scr.seeds)
+    a, b = _mc_spread(G, celf.seeds), _mc_spread(G, scr.seeds)
     print({"celf": a, "screened": b, "celf_sets": celf.evaluations, "screened_sets": scr.evaluations})
     assert b >= 0.98 * a
     assert scr.evaluations == 8 * k and scr.evaluations * 20 <= celf.evaluations

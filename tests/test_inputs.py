@@ -32,3 +32,39 @@ def test_erdos_renyi_and_ba_shapes():
     b = I.barabasi_albert(2000, 5, graph_seed=1)
     assert b.m == 2 * (2000 - 5) * 5
     _simple(b)
+
+
+def test_watts_strogatz_and_gnp():
+    w = I.watts_strogatz(1000, 10, 0.05, graph_seed=2)
+    assert w.m == 1000 * 10          # n k / 2 undirected edges, both directions stored
+    src = _simple(w)
+    fwd = set(zip(src.tolist(), w.col.tolist()))
+    assert all((v, u) in fwd for u, v in fwd)
+    g = I.erdos_renyi_gnp(2000, 0.002, graph_seed=1)
+    src = _simple(g)
+    assert abs(g.m / 2 - 0.002 * 2000 * 1999 / 2) < 5 * np.sqrt(0.002 * 2000 * 1999 / 2)
+
+
+def test_edge_weight_models():
+    g = I.erdos_renyi_m(500, 4000, graph_seed=3)
+    tv = I.ic_trivalency(g, graph_seed=1)
+    assert tv.dtype == np.float32 and set(np.unique(tv).tolist()) == {np.float32(0.1), np.float32(0.01),
+                                                                      np.float32(0.001)}
+    ur = I.ic_uniform_random(g, 1.0, graph_seed=1)
+    assert ur.dtype == np.float32 and ur.min() >= 0 and ur.max() < 1
+    wc = I.ic_weighted_cascade(g)
+    indeg = g.in_degree()
+    np.testing.assert_array_equal(wc, (np.float32(1.0) / indeg[g.col].astype(np.float32)))
+    lw = I.lt_weighted_cascade(g)
+    sums = np.bincount(g.col, weights=lw.astype(np.float64), minlength=g.n)
+    assert np.all(sums <= 2**32 - 1)
+
+
+def test_batch_items_shape():
+    off, seeds, tr, keys = I.batch_items(10_000, 4096, 1, 100, (256, 1024, 4096), graph_seed=1)
+    sizes = np.diff(off)
+    assert sizes.min() >= 1 and sizes.max() <= 100 and set(np.unique(tr).tolist()) == {256, 1024, 4096}
+    assert np.array_equal(keys, np.arange(1, 4097, dtype=np.uint64))
+    for i in range(0, 4096, 512):
+        s = seeds[off[i]:off[i + 1]]
+        assert np.unique(s).size == s.size
