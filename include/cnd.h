@@ -320,6 +320,11 @@ cnd_status cnd_lt_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *see
  * Host arrays throughout; a surrogate lives on its graph's device and owns
  * its working memory (about 0.5 KB per node).  The graph needs IC
  * probabilities.  Seed ids must lie in [0, n); duplicates count once.
+ *
+ * Not bit-reproducible: in-edge sums of high in-degree nodes are split over
+ * several warps and gradients are summed over blocks, both with fp32 atomic
+ * adds, so results can differ in their last bits between runs (and a bf16
+ * rounding of a sum by one unit).  Simulation results above are exact.
  */
 #define CND_SUR_N_PARAMS 18689
 typedef struct cnd_sur cnd_sur;
