@@ -659,6 +659,11 @@ def alg_bytes(model, s):
     return base + (16 if model == "ic" else 8) * s["updates"]
 
 
+def hbm_bound_rate(peak_gbs, edge_checks, alg_b):
+    """Edge checks per second of an expansion that moved only its algorithmic bytes at the HBM peak."""
+    return peak_gbs * 1e9 * edge_checks / alg_b if alg_b > 0 else None
+
+
 def run_ours(args):
     import torch
     import paper_2404_17059_gb300 as P
@@ -770,6 +775,9 @@ def run_ours(args):
                        "alg_bytes_per_launch": bpl,
                        "achieved_gbs": bpl / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None,
                        "expand_ms_per_step": exp_ms[model] / args.steps,
+                       "edge_checks_per_s_expand": r.edge_checks / (exp_ms[model] / args.steps * 1e-3)
+                       if exp_ms[model] > 0 else None,
+                       "hbm_bound_edge_checks_per_s": hbm_bound_rate(peak, r.edge_checks, alg_bytes(model, cs)),
                        "finalize_ms_per_step": fin_ms[model] / args.steps,
                        "passes": cs["passes"], "word_bits": cs["word_bits"], "levels": cs["levels"],
                        "counts": {k: cs[k] for k in ("frontier_slots", "work_items", "edges_scanned",

@@ -61,3 +61,9 @@ def test_select_models():
     assert wl.trials_per_step() == 1000
     with pytest.raises(SystemExit):
         bench.select_models(bench.make_workload("er1k"), "xx")
+
+
+def test_hbm_bound_rate():
+    # 1e9 edge checks moving 21.8e9 algorithmic bytes at 6,663.9 GB/s: 21.8e9 / 6663.9e9 s
+    assert bench.hbm_bound_rate(6663.9, 1e9, 21.8e9) == pytest.approx(1e9 / (21.8e9 / 6663.9e9))
+    assert bench.hbm_bound_rate(6663.9, 1e9, 0) is None
