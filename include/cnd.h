@@ -33,7 +33,7 @@
  *   LT.  Weights are uint32 fixed point: the weight w of edge u->v is the
  *   influence of u on v, and for every node the in-weights sum to at most
  *   2^32 - 1 (the fixed-point form of "sum <= 1", Sec. 2).  Node v becomes
- *   active in the step after the total weight of its active in-neighbours
+ *   active in the step after the summed weight of its active in-neighbours
  *   exceeds its threshold theta (a uint32): activation probability given total
  *   W is exactly W / 2^32, and a node with no active in-weight never activates.
  *
