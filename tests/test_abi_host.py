@@ -109,3 +109,11 @@ def test_lt_weights_wc_helper():
     assert np.all(np.bincount(g.col, weights=w, minlength=g.n) <= 0xFFFFFFFF)
     with pytest.raises(P.CndError):
         P.cnd_lt_weights_wc(g.n, np.array([0, g.n], dtype=np.int32))
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No CPU fallback: without the compiled library the binding raises instead of computing."""
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "libcnd.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        binding.load(build_if_missing=False)
