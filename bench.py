@@ -354,7 +354,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": wl.desc, "name": wl.name, "sample_per_step": desc},
+        "config": {"workload": wl.desc, "name": wl.name, "graph_sha256": wl.g.digest(), "sample_per_step": desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"each step: {desc}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -810,7 +810,7 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.desc, "name": wl.name, "graph_nodes": wl.g.n, "graph_edges": wl.g.m,
-                   "trials_per_step_per_rank": wl.trials_per_step(), "parallelism": f"trial-sharded x{world}",
+                   "graph_sha256": wl.g.digest(), "trials_per_step_per_rank": wl.trials_per_step(), "parallelism": f"trial-sharded x{world}",
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)"},
         "trials_per_s": trials_per_s,
         "graph_mode": {"ms_per_step": graph_ms, "value": checks_all / args.steps / (graph_ms / 1e3),
