@@ -67,3 +67,21 @@ def test_hbm_bound_rate():
     # 1e9 edge checks moving 21.8e9 algorithmic bytes at 6,663.9 GB/s: 21.8e9 / 6663.9e9 s
     assert bench.hbm_bound_rate(6663.9, 1e9, 21.8e9) == pytest.approx(1e9 / (21.8e9 / 6663.9e9))
     assert bench.hbm_bound_rate(6663.9, 1e9, 0) is None
+
+
+def test_reference_arm_json_contract():
+    """`bench.py --impl reference` (the oracle, CPU only) prints one JSON line with the contract's keys."""
+    import subprocess
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "er1k",
+                          "--steps", "1", "--warmup", "3"], capture_output=True, text=True, timeout=600, check=True)
+    lines = [ln for ln in out.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0
+    assert d["config"]["workload"] and d["config"]["graph_sha256"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
