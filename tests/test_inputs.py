@@ -68,3 +68,17 @@ def test_batch_items_shape():
     for i in range(0, 4096, 512):
         s = seeds[off[i]:off[i + 1]]
         assert np.unique(s).size == s.size
+
+
+def test_overlapping_hubs_structure():
+    g = I.overlapping_hubs(graph_seed=3)
+    assert g.n == 10 + 10 + 300 + 10 * 150 + 3000
+    out = g.out_degree()
+    shared = [set(g.col[g.row_ptr[h]:g.row_ptr[h + 1]].tolist()) & set(range(20, 320)) for h in range(10)]
+    assert all(s == set(range(20, 320)) for s in shared)      # the redundant hubs reach the same 300 nodes
+    for i, h in enumerate(range(10, 20)):                      # each small hub has 150 targets of its own
+        assert set(range(320 + 150 * i, 470 + 150 * i)) <= set(g.col[g.row_ptr[h]:g.row_ptr[h + 1]].tolist())
+    assert out[:10].min() > out[10:20].max() > out[20:].max()   # out-degree ranks the redundant hubs first
+    p = I.hub_probabilities(g)
+    src = g.src()
+    assert np.all(p[src < 20] == np.float32(0.9)) and np.all(p[src >= 20] == np.float32(0.02))
