@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import dataclasses
 import hashlib
+import os
 
 import numpy as np
 
@@ -27,6 +28,7 @@ __all__ = [
     "random_regular", "watts_strogatz", "path_graph", "out_star", "in_star",
     "ic_uniform", "ic_weighted_cascade", "ic_uniform_random", "ic_trivalency",
     "lt_weighted_cascade", "top_degree_seeds", "uniform_seeds", "batch_items",
+    "save_csr", "load_csr", "read_edge_list",
 ]
 
 LT_ONE = 0xFFFFFFFF  # largest total in-weight a node may carry (fixed point "1")
@@ -179,7 +181,6 @@ def _genlib():
     global _GEN_LIB
     if _GEN_LIB is None:
         import ctypes as C
-        import os
         import subprocess
         here = os.path.dirname(os.path.abspath(__file__))
         src = os.path.join(here, "gen", "rmat_gen.c")
@@ -209,7 +210,6 @@ def rmat(scale: int, n_samples: int, a: float = 0.57, b: float = 0.19, c: float 
     on (scale, n_samples, probabilities, graph_seed).  Self-loops and duplicate
     edges are dropped, so m <= n_samples; rows are sorted by target.
     """
-    import os
     if scale < 1 or scale > 30:
         raise ValueError("scale must be in 1..30")
     n = 1 << scale
@@ -440,6 +440,76 @@ def batch_items(n: int, n_items: int, size_lo: int, size_hi: int, trial_choices,
     seeds = np.concatenate([uniform_seeds(n, int(s), rng) for s in sizes]) if n_items else np.zeros(0, np.int32)
     rng_seeds = np.arange(1, n_items + 1, dtype=np.uint64)
     return seed_off, seeds.astype(np.int32), trials.astype(np.int32), rng_seeds
+
+
+# ----------------------------------------------------------------------------- graph files
+_CSR_MAGIC = b"CNDCSR01"
+
+
+def save_csr(g: Graph, path: str) -> str:
+    """Write ``g`` as a binary CSR file and return its digest (``Graph.digest``).
+
+    Layout (little-endian): 8-byte magic ``CNDCSR01``, n and m as int64, the
+    16 ASCII hex digits of the digest, row_ptr (int32, n + 1), col (int32, m).
+    """
+    d = g.digest()
+    with open(path, "wb") as f:
+        f.write(_CSR_MAGIC)
+        f.write(np.array([g.n, g.m], dtype="<i8").tobytes())
+        f.write(d.encode("ascii"))
+        f.write(np.ascontiguousarray(g.row_ptr, dtype="<i4").tobytes())
+        f.write(np.ascontiguousarray(g.col, dtype="<i4").tobytes())
+    return d
+
+
+def load_csr(path: str) -> Graph:
+    """Read a file written by ``save_csr``; ValueError if its magic, sizes or digest do not match."""
+    with open(path, "rb") as f:
+        raw = f.read()
+    head = len(_CSR_MAGIC) + 16 + 16
+    if len(raw) < head or raw[:len(_CSR_MAGIC)] != _CSR_MAGIC:
+        raise ValueError(f"{path}: not a CSR graph file")
+    n, m = (int(x) for x in np.frombuffer(raw, dtype="<i8", count=2, offset=len(_CSR_MAGIC)))
+    want = raw[len(_CSR_MAGIC) + 16:head].decode("ascii")
+    if n < 1 or m < 0 or len(raw) != head + 4 * (n + 1) + 4 * m:
+        raise ValueError(f"{path}: sizes do not match the header")
+    row_ptr = np.frombuffer(raw, dtype="<i4", count=n + 1, offset=head).astype(np.int32)
+    col = np.frombuffer(raw, dtype="<i4", count=m, offset=head + 4 * (n + 1)).astype(np.int32)
+    g = Graph(n=n, row_ptr=row_ptr, col=col, name=os.path.basename(path))
+    if g.digest() != want:
+        raise ValueError(f"{path}: digest mismatch (file {want}, contents {g.digest()})")
+    return g
+
+
+def read_edge_list(path: str, undirected: bool = False, comments: str = "#"):
+    """Graph from a whitespace-separated edge-list text file: one ``u v`` pair of integer ids per
+    line, lines starting with ``comments`` ignored (the format SNAP distributes its networks in).
+
+    Ids are relabelled 0..n-1 in increasing order of the original id; self-loops and repeated
+    edges are dropped; with ``undirected`` every edge is stored in both directions (as the
+    paper's benchmarks treat undirected networks, Sec. 4).  Returns (graph, ids) with ids[i]
+    the original id of node i.
+    """
+    pairs = []
+    with open(path) as f:
+        for line in f:
+            t = line.strip()
+            if not t or t.startswith(comments):
+                continue
+            a = t.split()
+            if len(a) < 2:
+                raise ValueError(f"{path}: malformed line {line!r}")
+            pairs.append((int(a[0]), int(a[1])))
+    e = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+    ids, inv = np.unique(e.ravel(), return_inverse=True)
+    inv = inv.reshape(-1, 2)
+    src, dst = inv[:, 0], inv[:, 1]
+    if undirected:
+        src, dst = np.concatenate([src, dst]), np.concatenate([dst, src])
+    keep = src != dst
+    n = max(int(ids.size), 1)
+    k = np.unique(src[keep] * n + dst[keep])
+    return csr_from_edges(n, k // n, k % n, name=os.path.basename(path)), ids
 
 
 # ----------------------------------------------------------------------------- surrogate inputs

@@ -1,5 +1,6 @@
 """Synthetic workload generators: the structural properties the workloads rely on."""
 import numpy as np
+import pytest
 
 from paper_2404_17059_gb300 import inputs as I
 
@@ -82,3 +83,33 @@ def test_overlapping_hubs_structure():
     p = I.hub_probabilities(g)
     src = g.src()
     assert np.all(p[src < 20] == np.float32(0.9)) and np.all(p[src >= 20] == np.float32(0.02))
+
+
+def test_csr_file_roundtrip_and_digest(tmp_path):
+    g = I.barabasi_albert(2000, 3, graph_seed=5)
+    p = str(tmp_path / "ba.csr")
+    d = I.save_csr(g, p)
+    h = I.load_csr(p)
+    assert d == g.digest() == h.digest() and h.n == g.n
+    assert np.array_equal(h.row_ptr, g.row_ptr) and np.array_equal(h.col, g.col)
+    raw = bytearray(open(p, "rb").read())
+    raw[-1] ^= 1                                              # one flipped bit in col
+    open(p, "wb").write(bytes(raw))
+    with pytest.raises(ValueError, match="digest"):
+        I.load_csr(p)
+    open(p, "wb").write(bytes(raw[:-4]))                      # truncated
+    with pytest.raises(ValueError, match="sizes"):
+        I.load_csr(p)
+
+
+def test_read_edge_list(tmp_path):
+    p = tmp_path / "edges.txt"
+    p.write_text("# a comment\n# FromNodeId\tToNodeId\n10 20\n20 30\n10 20\n30 30\n\n40 10\n")
+    g, ids = I.read_edge_list(str(p))
+    assert ids.tolist() == [10, 20, 30, 40] and g.n == 4
+    assert sorted(zip(g.src().tolist(), g.col.tolist())) == [(0, 1), (1, 2), (3, 0)]
+    u, ids_u = I.read_edge_list(str(p), undirected=True)
+    assert sorted(zip(u.src().tolist(), u.col.tolist())) == [(0, 1), (0, 3), (1, 0), (1, 2), (2, 1), (3, 0)]
+    p.write_text("1 2\n3\n")
+    with pytest.raises(ValueError, match="malformed"):
+        I.read_edge_list(str(p))
