@@ -263,7 +263,9 @@ cnd_status cnd_autotune(const cnd_graph *g, int32_t model, int32_t n_items, cons
  *   n_trials:       trials per evaluation, 1 .. 2^31 - 1.
  *   candidates:     host array of n_candidates distinct node ids, or NULL for
  *                   all nodes (n_candidates ignored).
- *   eval_batch:     0 = 64.  max_items: items per batched call, 0 = 8192.
+ *   eval_batch:     0 = 64.  max_items: items per batched call, 0 = 8192;
+ *                   also capped so that items x n_trials <= 2^28 (the
+ *                   per-trial spreads of one call stay within 1 GiB).
  *   sim:            engine settings for the batched calls (NULL = defaults;
  *                   its first_trial, a multiple of 64 as for every batched
  *                   call, is used; device_ptrs, stream and output pointers
