@@ -78,3 +78,16 @@ def test_candidates_restrict_the_choice(er):
     assert set(seeds.tolist()) <= set(cand)
     with pytest.raises(ValueError):
         im.celf("ic", er, len(cand) + 1, 8, 2, candidates=cand, ic_prob=p)
+
+
+def test_lt_celf_first_pick_is_the_exhaustive_best(er):
+    """Round 0 evaluates every candidate, so the first LT pick is argmax F({v}) (ties: lower id)
+    even though the LT objective over fixed trials need not be submodular."""
+    w = I.lt_weighted_cascade(er)
+    seeds, f, _ = im.celf("lt", er, 2, 48, 4, lt_weight=w)
+    single = np.array([_F("lt", er, [v], 48, 4, lt_weight=w) for v in range(er.n)])
+    assert seeds[0] == int(np.argmax(single)) and f[0] == single.max()
+    pair = np.array([_F("lt", er, [seeds[0], v], 48, 4, lt_weight=w) if v != seeds[0] else -1
+                     for v in range(er.n)])
+    assert f[1] <= pair.max()                          # the second pick's value is a real F(S + v)
+    assert f[1] == _F("lt", er, seeds[:2], 48, 4, lt_weight=w)
