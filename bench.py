@@ -4,15 +4,20 @@
 A step is one pass of the whole path over one batch of synthetic input (graph
 ingest happens once, before the timed region):
 
-  ba100k (default)  Barabasi-Albert n=100,000, 5 attachments, undirected edges
+  rmat24 (default)  the large configuration: R-MAT scale 24, edge factor 16 (2^28
+                    samples, deduplicated: 263,430,501 edges); IC with p = 0.01
+                    and LT with weighted-cascade weights; 100 highest-degree
+                    seeds; 100,000 trials per model.  A step is one IC call on
+                    2,048 trials and one LT call on 1,024 trials (--trials,
+                    --lt-trials), each a contiguous range of trial ids; the
+                    ranges rotate through the 100,000 from step to step
+                    (first_trial), so every step does full trials and no work
+                    is skipped.  --scale changes the scale (ncu captures).
+  ba100k            Barabasi-Albert n=100,000, 5 attachments, undirected edges
                     stored both ways (999,950 directed edges); weighted-cascade
                     IC probabilities (fp32) and LT weights (uint32 fixed point);
                     the 50 highest-degree nodes as seeds; one IC and one LT
                     simulation of 10,000 trials each.
-  rmat24            R-MAT scale 24, edge factor 16 (2^28 samples, deduplicated:
-                    263,430,501 edges); IC with p = 0.01 and LT with weighted-
-                    cascade weights; 100 highest-degree seeds; a sample of the
-                    100,000 trials per model (--trials, default 16384).
   rmat20batch       R-MAT scale 20, 2^24 samples (16,084,954 edges), p ~ U[0,0.1)
                     per edge; one batched IC call over the first K of 4,096 seed
                     sets (|S| ~ U{1..100}, trials from {256, 1024, 4096}).
@@ -78,19 +83,23 @@ from paper_2404_17059_gb300 import inputs as I  # noqa: E402
 METRIC = "IC/LT edge checks/sec and trials/sec at 1 GB300 (% of HBM peak); surrogate vs MC greedy speedup"
 UNIT = "edge_checks/s"
 FALLBACK_HBM_GBS = 6800.0
-# Philox-4x32-10 = 10 rounds x two 32x32->64-bit products = 40 32-bit multiply results per call;
-# 152 SMs x 64 integer multiplies per clock x 2.07 GHz (maximum SM clock)
-PHILOX_PEAK_G = 152 * 64 * 2.07 / 40
 
 
 # ----------------------------------------------------------------------------- workloads
 class Workload:
-    """A graph, its per-model edge data, seeds and the calls of one step."""
+    """A graph, its per-model edge data, seeds and the calls of one step.
 
-    def __init__(self, name, desc, g, models, seeds=None, trials=0, rng_seed=1, batch=None, cpu=None):
+    trials: {"ic": T, "lt": T} trials per model per step.  total: the configuration's trial count per
+    model; when it exceeds a step's trials, step i simulates the contiguous range of trial ids
+    [r T, (r + 1) T) with r = (i * world + rank) mod floor(total / T), so that successive steps (and
+    ranks) rotate through the configuration's trials via first_trial."""
+
+    def __init__(self, name, desc, g, models, seeds=None, trials=None, rng_seed=1, batch=None, cpu=None, total=0):
         self.name, self.desc, self.g = name, desc, g
         self.models = models          # {"ic": p or None, "lt": w or None}
-        self.seeds, self.trials, self.rng_seed = seeds, trials, rng_seed
+        self.seeds, self.rng_seed = seeds, rng_seed
+        self.trials = dict(trials or {})
+        self.total = total
         self.batch = batch            # (seed_off, seeds, trials, keys) or None
         self.cpu = cpu or {}          # CPU-oracle sample sizes
 
@@ -103,16 +112,23 @@ class Workload:
         k = len(trials)
         return seed_off, seeds, trials, keys, k
 
-    def calls(self, P, G, seeds_arg, rank, stats=0, graph=0):
+    def first_trial(self, model, step, rank, world):
+        T = self.trials[model]
+        span = ((T + 63) // 64) * 64
+        if self.total <= T:
+            return rank * span  # every step simulates the whole configuration; ranks take their own ids
+        return ((step * world + rank) % (self.total // span)) * span
+
+    def calls(self, P, G, seeds_arg, rank, stats=0, graph=0, step=0, world=1):
         """One step: a list of (model, SimResult)."""
         out = []
         if self.batch is None:
-            first = rank * (((self.trials + 63) // 64) * 64)
             for model in ("ic", "lt"):
                 if self.models.get(model) is None:
                     continue
                 f = P.cnd_ic_simulate_ex if model == "ic" else P.cnd_lt_simulate_ex
-                out.append((model, f(G, seeds_arg, self.trials, self.rng_seed, first_trial=first, edge_checks=True,
+                out.append((model, f(G, seeds_arg, self.trials[model], self.rng_seed,
+                                     first_trial=self.first_trial(model, step, rank, world), edge_checks=True,
                                      stats=stats, graph=graph)))
         else:
             seed_off, _, trials, keys = self.batch
@@ -125,14 +141,14 @@ class Workload:
 
     def trials_per_step(self):
         if self.batch is None:
-            return self.trials * sum(1 for m in ("ic", "lt") if self.models.get(m) is not None)
+            return sum(self.trials[m] for m in ("ic", "lt") if self.models.get(m) is not None)
         return int(np.asarray(self.batch[2], dtype=np.int64).sum())
 
     def io_bytes(self):
         """Bytes copied in / out per step by the host-pointer calls."""
         if self.batch is None:
-            k = sum(1 for m in ("ic", "lt") if self.models.get(m) is not None)
-            return k * self.seeds.size * 4, k * (self.trials * 4 + self.g.n * 4 + 8)
+            ms = [m for m in ("ic", "lt") if self.models.get(m) is not None]
+            return len(ms) * self.seeds.size * 4, sum(self.trials[m] * 4 + self.g.n * 4 + 8 for m in ms)
         return self.batch[1].size * 4, self.trials_per_step() * 4 + 8
 
 
@@ -145,31 +161,37 @@ def select_models(wl: Workload, models: str) -> Workload:
     return wl
 
 
-def make_workload(name: str, trials: int = 0, items: int = 0) -> Workload:
+RMAT24_TRIALS = {"ic": 2048, "lt": 1024}  # trials per model per step of the R-MAT workload (of 100,000)
+
+
+def make_workload(name: str, trials: int = 0, items: int = 0, lt_trials: int = 0, scale: int = 24) -> Workload:
     if name == "ba100k":
         g = I.barabasi_albert(100_000, 5, graph_seed=1)
-        T = trials or 10_000
+        T = {"ic": trials or 10_000, "lt": lt_trials or trials or 10_000}
         return Workload(
             name, f"BA n=100000 m_attach=5 symmetrised ({g.m} directed edges), weighted-cascade IC (fp32 "
-                  f"p=1/indeg) and LT (uint32 floor((2^32-1)/indeg)), 50 top-degree seeds, {T} trials per model, "
-                  "rng_seed=1",
+                  f"p=1/indeg) and LT (uint32 floor((2^32-1)/indeg)), 50 top-degree seeds, {T['ic']} IC and "
+                  f"{T['lt']} LT trials per step, rng_seed=1",
             g, {"ic": I.ic_weighted_cascade(g), "lt": I.lt_weighted_cascade(g)}, seeds=I.top_degree_seeds(g, 50),
-            trials=T, cpu={"ic": 2048, "lt": 1536})
+            trials=T, cpu={"ic": 2048, "lt": 1536}, total=10_000)
     if name == "er1k":
         g = I.erdos_renyi_m(1000, 10_000, graph_seed=1)
-        T = trials or 1000
+        T = {"ic": trials or 1000, "lt": lt_trials or trials or 1000}
         return Workload(
-            name, f"directed ER n=1000 m=10000, IC p=0.1, LT weighted cascade, 10 uniform seeds, {T} trials per model",
+            name, f"directed ER n=1000 m=10000, IC p=0.1, LT weighted cascade, 10 uniform seeds, {T['ic']} IC and "
+                  f"{T['lt']} LT trials per step",
             g, {"ic": I.ic_uniform(g, 0.1), "lt": I.lt_weighted_cascade(g)}, seeds=I.uniform_seeds(g.n, 10, 1),
-            trials=T, cpu={"ic": 1000, "lt": 1000})
+            trials=T, cpu={"ic": 1000, "lt": 1000}, total=1000)
     if name == "rmat24":
-        g = I.rmat(24, 16 << 24, graph_seed=1)
-        T = trials or 16384
+        g = I.rmat(scale, 16 << scale, graph_seed=1)
+        T = {"ic": trials or RMAT24_TRIALS["ic"], "lt": lt_trials or RMAT24_TRIALS["lt"]}
         return Workload(
-            name, f"R-MAT scale 24 edge factor 16 (a,b,c,d=.57,.19,.19,.05; {g.m} directed edges after dedup), IC "
-                  f"p=0.01 and LT weighted cascade, 100 top-degree seeds, {T} of the 100000 trials per model",
+            name, f"R-MAT scale {scale} edge factor 16 (a,b,c,d=.57,.19,.19,.05; {g.m} directed edges after dedup), "
+                  f"IC p=0.01 and LT weighted cascade, 100 top-degree seeds, 100000 trials per model, rng_seed=1; "
+                  f"each step simulates a contiguous range of {T['ic']} IC and {T['lt']} LT trial ids, the ranges "
+                  f"rotating through the 100000 via first_trial",
             g, {"ic": I.ic_uniform(g, 0.01), "lt": I.lt_weighted_cascade(g)}, seeds=I.top_degree_seeds(g, 100),
-            trials=T, cpu={"ic": 16, "lt": 16})
+            trials=T, cpu={"ic": 16, "lt": 16}, total=100_000)
     if name == "rmat20batch":
         g = I.rmat(20, 1 << 24, graph_seed=1)
         so, seeds, tr, keys = I.batch_items(g.n, 4096, 1, 100, (256, 1024, 4096), graph_seed=1)
@@ -337,7 +359,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    wl = select_models(make_workload(args.workload, args.trials, args.items), args.models)
+    wl = select_models(make_workload(args.workload, args.trials, args.items, args.lt_trials, args.scale),
+                       args.models)
     if args.ref_trials:
         for m, n in zip(("ic", "lt"), args.ref_trials):
             if m in wl.cpu:
@@ -648,15 +671,28 @@ def run_surrogate24(args):
 
 
 # ----------------------------------------------------------------------------- our arm
-KERNEL = {"ic": "k_push<0>", "lt": "k_push<1>"}
+def kernel_name(model, s):
+    """The expansion kernel a counted call ran: k_push<0> (IC), k_push<1> (LT, per-trial in-weight
+    sums) or k_push<2> (LT, counting form)."""
+    if model == "ic":
+        return "k_push<0>"
+    return "k_push<2>" if s.get("lt_counters") else "k_push<1>"
 
 
 def alg_bytes(model, s):
     """Bytes the expansion kernel must move, from its own work counters: 8 per work item (row_ptr pair),
     8 per frontier word loaded, 8 per edge read ({col, thr}), 8 per word check (the target's word) and
-    16 per IC word update (vis and next read-modify-write) or 8 per LT accumulator add."""
+    16 per IC word update (vis and next read-modify-write), 8 per LT accumulator add (4-byte read-modify-
+    write) or 16 per counter-plane update of the LT counting form (8-byte read-modify-write)."""
     base = 8 * s["work_items"] + 8 * s["frontier_words"] + 8 * s["edges_scanned"] + 8 * s["word_checks"]
-    return base + (16 if model == "ic" else 8) * s["updates"]
+    if model == "ic":
+        return base + 16 * s["updates"]
+    return base + (16 if s.get("lt_counters") else 8) * s["updates"]
+
+
+def traffic_key(wl, args):
+    """Workload key of the ncu traffic records: the R-MAT workload names its scale."""
+    return f"rmat{args.scale}" if wl.name == "rmat24" else wl.name
 
 
 def hbm_bound_rate(peak_gbs, edge_checks, alg_b):
@@ -679,7 +715,8 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
 
-    wl = select_models(make_workload(args.workload, args.trials, args.items), args.models)
+    wl = select_models(make_workload(args.workload, args.trials, args.items, args.lt_trials, args.scale),
+                       args.models)
     if wl.batch is not None and world > 1:
         # each rank its own seed sets: a disjoint slice of the 4096-item list
         g = wl.g
@@ -690,16 +727,20 @@ def run_ours(args):
     G = wl.create(P)
     seeds_d = torch.as_tensor(wl.host_seeds(), device=dev)
     if args.profile_calls:
-        out = {m: r.stats for m, r in wl.calls(P, G, seeds_d, rank, stats=CND_STATS_COUNT)}
+        out = {m: r.stats for m, r in wl.calls(P, G, seeds_d, rank, stats=CND_STATS_COUNT, world=world)}
         torch.cuda.synchronize()
         print(json.dumps({"profile_calls": out, "workload": wl.name, "trials": wl.trials, "src": source_hash()}))
         return 0
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    counted = dict(wl.calls(P, G, seeds_d, rank, stats=CND_STATS_COUNT))  # work counts (untimed)
+    # step indices: 0 the counted call, then warm-up, timed, graph-mode and end-to-end steps, so that
+    # single-seed-set workloads rotate through their trial ranges (Workload.first_trial)
+    step = 0
+    counted = dict(wl.calls(P, G, seeds_d, rank, stats=CND_STATS_COUNT, step=step, world=world))  # work counts
     for _ in range(args.warmup):
-        wl.calls(P, G, seeds_d, rank)
+        step += 1
+        wl.calls(P, G, seeds_d, rank, step=step, world=world)
     torch.cuda.synchronize()
 
     if dist:
@@ -707,13 +748,14 @@ def run_ours(args):
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     checks = launches = 0
-    exp_ms, exp_n, fin_ms = {}, {}, {}
+    exp_ms, exp_n, fin_ms, set_ms, mchecks = {}, {}, {}, {}, {}
     wall0 = time.perf_counter()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
+            step += 1
             flush.zero_()  # L2 flush (256 MiB write) outside the timed events
             ev[i][0].record(stream)
-            res = wl.calls(P, G, seeds_d, rank, stats=CND_STATS_TIMING)
+            res = wl.calls(P, G, seeds_d, rank, stats=CND_STATS_TIMING, step=step, world=world)
             ev[i][1].record(stream)
             for model, r in res:
                 checks += r.edge_checks
@@ -721,6 +763,8 @@ def run_ours(args):
                 exp_ms[model] = exp_ms.get(model, 0.0) + r.stats["expand_ms"]
                 exp_n[model] = exp_n.get(model, 0) + r.stats["expand_launches"]
                 fin_ms[model] = fin_ms.get(model, 0.0) + r.stats["finalize_ms"]
+                set_ms[model] = set_ms.get(model, 0.0) + r.stats["setup_ms"]
+                mchecks[model] = mchecks.get(model, 0) + r.edge_checks
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if dist:
@@ -738,23 +782,28 @@ def run_ours(args):
     value = checks_all / (total_ms / 1e3)
     trials_per_s = world * wl.trials_per_step() * args.steps / (total_ms / 1e3)
 
-    # ---- the same steps as one CUDA-graph launch per call (device-side step loop; no per-kernel events)
-    ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
+    # ---- a few more steps as one CUDA-graph launch per call (device-side step loop; no per-kernel events)
+    ng = max(1, args.graph_steps)
+    ev_g = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(ng)]
+    g_checks = 0
+    for i in range(ng):
+        step += 1
         flush.zero_()
         ev_g[i][0].record(stream)
-        wl.calls(P, G, seeds_d, rank, graph=1)
+        g_checks += sum(r.edge_checks for _, r in wl.calls(P, G, seeds_d, rank, graph=1, step=step, world=world))
         ev_g[i][1].record(stream)
     torch.cuda.synchronize()
-    graph_ms = sum(a.elapsed_time(b) for a, b in ev_g) / args.steps
+    graph_ms = sum(a.elapsed_time(b) for a, b in ev_g)
 
-    # ---- end to end through the host-pointer API
+    # ---- end to end through the host-pointer API (seeds in, spreads / counts / edge checks out)
     seeds_h = wl.host_seeds()
+    ne = max(1, args.e2e_steps)
     torch.cuda.synchronize()
     e2e_checks = 0
     t0 = time.perf_counter()
-    for i in range(args.steps):
-        e2e_checks += sum(r.edge_checks for _, r in wl.calls(P, G, seeds_h, rank))
+    for i in range(ne):
+        step += 1
+        e2e_checks += sum(r.edge_checks for _, r in wl.calls(P, G, seeds_h, rank, step=step, world=world))
     e2e_s = time.perf_counter() - t0
     h2d, d2h = wl.io_bytes()
 
@@ -763,43 +812,55 @@ def run_ours(args):
     if rank != 0:
         return 0
 
-    # ---- roofline of the dominant expansion kernel (algorithmic bytes counted by the kernels)
+    # ---- roofline of the dominant expansion kernel: algorithmic bytes per edge check counted by the
+    # kernels in the counted call, times the timed steps' edge checks, over the timed expansion time
     peak, peak_kind = measured_peak()
     kern = {}
     for model, r in counted.items():
         cs = r.stats
-        n_l = max(1, cs["expand_launches"])
-        bpl = alg_bytes(model, cs) / n_l
-        avg_ms = exp_ms[model] / max(1, exp_n[model])
-        kern[model] = {"kernel": KERNEL[model], "launches_per_step": n_l, "avg_launch_ms": avg_ms,
-                       "alg_bytes_per_launch": bpl,
-                       "achieved_gbs": bpl / (avg_ms * 1e-3) / 1e9 if avg_ms > 0 else None,
+        name = kernel_name(model, cs)
+        b_per_check = alg_bytes(model, cs) / max(1, r.edge_checks)
+        tb = b_per_check * mchecks[model]  # algorithmic bytes of the timed steps
+        n_l = max(1, exp_n[model])
+        kern[model] = {"kernel": name, "launches_per_step": n_l / args.steps, "avg_launch_ms": exp_ms[model] / n_l,
+                       "alg_bytes_per_launch": tb / n_l, "alg_bytes_per_edge_check": b_per_check,
+                       "achieved_gbs": tb / (exp_ms[model] * 1e-3) / 1e9 if exp_ms[model] > 0 else None,
                        "expand_ms_per_step": exp_ms[model] / args.steps,
-                       "edge_checks_per_s_expand": r.edge_checks / (exp_ms[model] / args.steps * 1e-3)
+                       "edge_checks_per_step": mchecks[model] / args.steps,
+                       "edge_checks_per_s_expand": mchecks[model] / (exp_ms[model] * 1e-3)
                        if exp_ms[model] > 0 else None,
                        "hbm_bound_edge_checks_per_s": hbm_bound_rate(peak, r.edge_checks, alg_bytes(model, cs)),
                        "finalize_ms_per_step": fin_ms[model] / args.steps,
+                       "setup_ms_per_step": set_ms[model] / args.steps,
+                       "lt_counters": cs.get("lt_counters", 0) if model == "lt" else None,
                        "passes": cs["passes"], "word_bits": cs["word_bits"], "levels": cs["levels"],
-                       "counts": {k: cs[k] for k in ("frontier_slots", "work_items", "edges_scanned",
-                                                     "frontier_words", "word_checks", "draws", "updates")}}
+                       "counted_call": {"edge_checks": r.edge_checks,
+                                        **{k: cs[k] for k in ("frontier_slots", "work_items", "edges_scanned",
+                                                              "frontier_words", "word_checks", "draws", "updates")}}}
     dom = max(kern, key=lambda k: kern[k]["expand_ms_per_step"])
     K = kern[dom]
     ach = K["achieved_gbs"] or 0.0
-    wc_per_launch = K["counts"]["word_checks"] / max(1, K["launches_per_step"])
+    cc = K["counted_call"]
+    wc_per_launch = cc["word_checks"] / max(1, cc["edge_checks"]) * K["edge_checks_per_step"] / K["launches_per_step"]
     roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": ncu_traffic(K["kernel"], wl.name, wc_per_launch), "kernel": K["kernel"],
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback"}
-    # the IC push draws a Philox-4x32-10 block (4 coins) per candidate 4-trial block: where its draws
-    # outweigh its bytes it is bound by integer multiplies, and its roofline is the Philox rate
+            "traffic": ncu_traffic(K["kernel"], traffic_key(wl, args), wc_per_launch), "kernel": K["kernel"],
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)" if peak_kind == "measured"
+            else "fallback"}
+    # the IC push draws Philox-4x32-10 blocks for its coins: where its draws outweigh its bytes it is
+    # bound by integer arithmetic, and its roofline is the Philox rate, measured here on this device
+    # with the engine's own generator (cnd_philox_rate)
     alu = None
     if "ic" in kern:
         KI = kern["ic"]
-        # counts are those of one (counted) call; the expansion time is per step (one call per model)
-        draws_s = KI["counts"]["draws"] / max(1e-9, KI["expand_ms_per_step"] * 1e-3)
-        alu = {"bound": "alu", "achieved": draws_s / 1e9, "peak": PHILOX_PEAK_G, "unit": "G Philox/s",
-               "frac": draws_s / 1e9 / PHILOX_PEAK_G, "kernel": KI["kernel"],
-               "peak_source": "derived: 152 SMs x 64 32-bit integer multiplies/clk x 2.07 GHz / 40 per Philox call",
-               "draws_per_word_check": KI["counts"]["draws"] / max(1, KI["counts"]["word_checks"])}
+        pk, pk_ms = P.cnd_philox_rate(4096)
+        pk_g = pk / 1e9
+        draws_per_check = KI["counted_call"]["draws"] / max(1, KI["counted_call"]["edge_checks"])
+        draws_s = draws_per_check * mchecks["ic"] / max(1e-9, exp_ms["ic"] * 1e-3)
+        alu = {"bound": "alu", "achieved": draws_s / 1e9, "peak": pk_g, "unit": "G Philox/s",
+               "frac": draws_s / 1e9 / pk_g, "kernel": KI["kernel"],
+               "peak_source": f"measured: cnd_philox_rate on this device ({pk_ms:.1f} ms launch; "
+                              f"{torch.cuda.get_device_properties(dev).multi_processor_count} SMs)",
+               "draws_per_word_check": KI["counted_call"]["draws"] / max(1, KI["counted_call"]["word_checks"])}
         if dom == "ic" and alu["frac"] > roof["frac"]:
             roof, alu = dict(alu, traffic=roof["traffic"], hbm_view={k: roof[k] for k in ("achieved", "peak",
                                                                                      "unit", "frac")}), roof
@@ -810,15 +871,17 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": wl.desc, "name": wl.name, "graph_nodes": wl.g.n, "graph_edges": wl.g.m,
-                   "graph_sha256": wl.g.digest(), "trials_per_step_per_rank": wl.trials_per_step(), "parallelism": f"trial-sharded x{world}",
+                   "graph_sha256": wl.g.digest(), "trials_per_step_per_rank": wl.trials_per_step(),
+                   "trials_per_model_per_step": wl.trials, "parallelism": f"trial-sharded x{world}",
+                   "call_mode": "host step loop (the default), CUDA events around each expansion launch",
                    "l2": "flushed between timed steps (256 MiB write, outside the step events)"},
         "trials_per_s": trials_per_s,
-        "graph_mode": {"ms_per_step": graph_ms, "value": checks_all / args.steps / (graph_ms / 1e3),
-                       "note": "same steps, one CUDA-graph launch per call (opts.graph=1)"},
+        "graph_mode": {"steps": ng, "ms_per_step": graph_ms / ng, "value": g_checks * world / (graph_ms / 1e3),
+                       "note": "further steps (their own trial ranges), one CUDA-graph launch per call (opts.graph=1)"},
         "edge_checks_per_step": checks_all / args.steps,
         "clocks": clk.summary(),
         "e2e": {"value": world * e2e_checks / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": ne},
         "gpu_launches": launches,
         "roofline": roof,
         "roofline_other": alu,
@@ -837,10 +900,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", default="ba100k",
+    ap.add_argument("--workload", default="rmat24",
                     choices=["ba100k", "rmat24", "rmat20batch", "er1k", "celf_rr7", "surrogate", "surrogate24",
                              "table1", "rmat20batch_full"])
-    ap.add_argument("--scale", type=int, default=24, help="surrogate24: R-MAT scale")
+    ap.add_argument("--scale", type=int, default=24, help="rmat24 / surrogate24: R-MAT scale (edge factor 16)")
     ap.add_argument("--models", default="ic,lt", help="single-seed-set workloads: models to run (ic, lt or both)")
     ap.add_argument("--pairs", type=int, default=200_000, help="surrogate: training pairs")
     ap.add_argument("--k", type=int, default=50, help="surrogate: seeds to choose")
@@ -849,12 +912,16 @@ def main():
     ap.add_argument("--screen-mode", default="onehop", choices=["gradient", "onehop"],
                     help="surrogate: first score of the screen")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--trials", type=int, default=0, help="override the workload's trials per model")
+    ap.add_argument("--trials", type=int, default=0, help="override the workload's (IC) trials per step")
+    ap.add_argument("--lt-trials", type=int, default=0, help="override the workload's LT trials per step")
+    ap.add_argument("--graph-steps", type=int, default=3, help="extra steps timed in CUDA-graph mode")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="extra steps timed end to end through host pointers")
     ap.add_argument("--items", type=int, default=0, help="rmat20batch: seed sets per step (default 64)")
     ap.add_argument("--profile-calls", action="store_true",
                     help="run one counted step only (for ncu captures of its launches)")
-    ap.add_argument("--ref-trials", type=int, nargs=2, default=(384, 256),
-                    help="IC and LT trials per reference step (single-seed-set workloads)")
+    ap.add_argument("--ref-trials", type=int, nargs=2, default=None,
+                    help="IC and LT trials per reference step (single-seed-set workloads; default: the "
+                         "workload's CPU-baseline sample)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

@@ -100,8 +100,14 @@ typedef struct cnd_sim_stats {
     int64_t frontier_words;    /* frontier words loaded by the expansion kernels */
     int64_t word_checks;       /* (edge, word) pairs with frontier bits: target word read */
     int64_t draws;             /* Philox blocks drawn (IC coins; LT thresholds) */
-    int64_t updates;           /* IC: target words that gained bits; LT: accumulator adds */
+    int64_t updates;           /* IC: (edge, target word) pairs with live coins for inactive trials
+                                  (each or-ed into the target's words); LT: accumulator adds, or
+                                  counter-plane updates in the counting form */
     int64_t pull_steps;        /* expansion steps run in the pull direction */
+    int32_t lt_counters;       /* 1: LT ran in the counting form (see lt_accumulate) */
+    int32_t pad0;
+    double setup_ms;           /* CUDA-event time of the per-pass set-up: state zero fills and, in
+                                  the counting form, the counter start values (CND_STATS_TIMING) */
 } cnd_sim_stats;
 
 /* Options of the *_ex entry points.  Zero-initialise (cnd_sim_opts_init). */
@@ -143,7 +149,13 @@ typedef struct cnd_sim_opts {
     int32_t autotune;          /* 1: take word_bits, chunk_edges, pull_permille and graph from the
                                   autotuner's cache for this graph, model and problem size class,
                                   tuning (cnd_autotune on a sample of this call) on a miss */
-    int32_t reserved2;
+    int32_t lt_accumulate;     /* LT only.  0 (default): where every node's non-zero in-weights are
+                                  equal (the weighted cascade), keep per (node, trial) a count of
+                                  active in-neighbours, bit-sliced over ceil(log2(k_v + 1)) planes
+                                  of 64 trials (k_v the node's in-edges of non-zero weight), since
+                                  k * w_v > theta <=> k > floor(theta / w_v); elsewhere, and with 1,
+                                  keep the 32-bit in-weight sum per (node, trial).  Both compute
+                                  exactly the same results */
     int64_t reserved[1];
 } cnd_sim_opts;
 
@@ -434,6 +446,17 @@ cnd_status cnd_lt_weights_wc(int32_t n, int32_t m, const int32_t *col, uint32_t 
  * i < count.  Host arrays of 4*count uint32 each.
  */
 cnd_status cnd_philox4x32_10(uint64_t rng_seed, const uint32_t *ctr, int64_t count, uint32_t *out);
+
+/*
+ * Throughput of the engine's Philox4x32-10 (the generator above) on the current device, for the
+ * roofline of the coin-drawing kernels (measurement only; the paper has no counterpart): one
+ * launch of as many 256-thread blocks as are resident on all SMs, each thread computing 2 x iters
+ * blocks in registers with the same code and precomputed round keys the expansion kernels use,
+ * timed with CUDA events on `stream` (NULL = legacy default stream) after one short warm-up
+ * launch.  *blocks_per_s_out = Philox blocks per second; ms_out (may be NULL) = the launch time.
+ * iters >= 1 (about 4096 keeps the launch near 100 ms on a GB300).  Allocates 1 KB per block.
+ */
+cnd_status cnd_philox_rate(int32_t iters, void *stream, double *blocks_per_s_out, double *ms_out);
 
 /*
  * Allocation-free IC simulation.  The paper has no counterpart: this entry

@@ -28,7 +28,7 @@ EXPORTS = (
     "cnd_lt_simulate_batch", "cnd_autotune", "cnd_im_opts_init", "cnd_ic_im_celf", "cnd_lt_im_celf",
     "cnd_sur_create", "cnd_sur_destroy", "cnd_sur_set_params", "cnd_sur_get_params", "cnd_sur_forward",
     "cnd_sur_loss_grad", "cnd_sur_adam", "cnd_sur_scores", "cnd_sur_train_opts_init", "cnd_sur_train",
-    "cnd_ic_im_screened", "cnd_sur_onehop",
+    "cnd_ic_im_screened", "cnd_sur_onehop", "cnd_philox_rate",
 )
 CND_SUR_N_PARAMS = 18689
 
@@ -61,6 +61,9 @@ class cnd_sim_stats(C.Structure):
         ("draws", C.c_int64),
         ("updates", C.c_int64),
         ("pull_steps", C.c_int64),
+        ("lt_counters", C.c_int32),
+        ("pad0", C.c_int32),
+        ("setup_ms", C.c_double),
     ]
 
     def as_dict(self):
@@ -86,7 +89,7 @@ class cnd_sim_opts(C.Structure):
         ("defer_steps", C.c_int32),
         ("graph", C.c_int32),
         ("autotune", C.c_int32),
-        ("reserved2", C.c_int32),
+        ("lt_accumulate", C.c_int32),
         ("reserved", C.c_int64 * 1),
     ]
 
@@ -186,6 +189,8 @@ def load(build_if_missing: bool = True):
         L.cnd_lt_weights_wc.restype = i32
         L.cnd_philox4x32_10.argtypes = [u64, vp, i64, vp]
         L.cnd_philox4x32_10.restype = i32
+        L.cnd_philox_rate.argtypes = [i32, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.cnd_philox_rate.restype = i32
         L.cnd_ic_simulate_noalloc.argtypes = [vp, vp, i32, i64, u64, vp, vp, vp]
         L.cnd_ic_simulate_noalloc.restype = i32
         L.cnd_last_error.argtypes = []
@@ -273,7 +278,7 @@ class SimResult:
 def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=True, node_count=True,
               first_trial=0, max_levels=0, direction="auto", word_bits=0, level_counts_len=0,
               edge_checks=False, pull_permille=0, chunk_edges=0, timeout_s=0.0, stream=None, stats=0,
-              defer_bits=0, defer_steps=0, graph=0, autotune=0):
+              defer_bits=0, defer_steps=0, graph=0, autotune=0, lt_accumulate=0):
     L = load()
     n_trials = int(n_trials)
     dev = _is_torch_cuda(seeds)
@@ -321,6 +326,7 @@ def _simulate(fn_name, g: CndGraph, seeds, n_trials, rng_seed, *, ex, spread=Tru
         o.defer_steps = int(defer_steps)
         o.graph = int(graph)
         o.autotune = int(autotune)
+        o.lt_accumulate = int(lt_accumulate)
         o.timeout_s = float(timeout_s)
         stt = None
         if stats:
@@ -369,6 +375,14 @@ def cnd_philox4x32_10(rng_seed, ctr) -> np.ndarray:
     out = np.empty_like(ctr)
     _check(load().cnd_philox4x32_10(C.c_uint64(rng_seed), _np_ptr(ctr), int(ctr.shape[0]), _np_ptr(out)))
     return out
+
+
+def cnd_philox_rate(iters=4096, stream=None):
+    """Measured Philox4x32-10 blocks per second of the engine's generator on the current device
+    (returns (blocks_per_s, launch_ms))."""
+    r, ms = C.c_double(), C.c_double()
+    _check(load().cnd_philox_rate(int(iters), stream, C.byref(r), C.byref(ms)))
+    return r.value, ms.value
 
 
 def cnd_ic_simulate_noalloc(g, seeds, n_trials, rng_seed, spread_out, node_count_out, stream=None) -> int:

@@ -89,6 +89,13 @@ struct cnd_graph_dev {
     uint4 *in_edge = nullptr;       // [m] {src, edge id, IC threshold, LT weight}
     int32_t max_out_degree = 0;
     int num_sms = 0;
+    // LT counting form, set when every node's non-zero in-weights are equal (the weighted
+    // cascade): node v keeps, per 64-trial word, L_v = bits(k_v) bit-sliced counter planes
+    // (k_v its in-edges of non-zero weight) at planes [cnt_off[v] * B + w * L_v, + L_v)
+    uint2 *lt_cnt_edge = nullptr;   // [m] {col, (cnt_off[col] << 5) | L_col}, 0 for a zero-weight edge
+    int32_t *lt_cnt_off = nullptr;  // [n+1] prefix sums of L_v
+    uint32_t *lt_unit_w = nullptr;  // [n] the common in-weight of v (0: no in-edge of non-zero weight)
+    int64_t lt_planes = 0;          // sum of L_v (planes per word column)
 };
 
 // ---------------------------------------------------------------- errors

@@ -5,6 +5,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -41,6 +42,17 @@ __global__ void k_build_lt_edges(int32_t m, const int32_t *__restrict__ col, con
         out[e] = make_uint2((uint32_t)col[e], w[e]);
 }
 
+// Counting-form LT edges: {col, tag}; tag = (first plane of the target << 5) | its plane count,
+// or 0 for an edge of zero weight (it adds nothing, so the push skips it).
+__global__ void k_build_lt_cnt_edges(int32_t m, const int32_t *__restrict__ col, const uint32_t *__restrict__ w,
+                                     const int32_t *__restrict__ cnt_off, uint2 *__restrict__ out) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = col[e];
+        const uint32_t L = (uint32_t)(cnt_off[v + 1] - cnt_off[v]);
+        out[e] = make_uint2((uint32_t)v, w[e] ? (((uint32_t)cnt_off[v] << 5) | L) : 0u);
+    }
+}
+
 // in_edge[k] = {src, edge id, IC threshold, LT weight} for the k-th in-edge.
 __global__ void k_build_in_edges(int32_t m, const int32_t *__restrict__ in_src, const int32_t *__restrict__ in_eid,
                                  const uint2 *__restrict__ ic, const uint2 *__restrict__ lt, uint4 *__restrict__ out) {
@@ -58,12 +70,29 @@ __global__ void k_philox(uint32_t k0, uint32_t k1, const uint4 *__restrict__ ctr
     }
 }
 
+// Philox throughput probe: every thread computes `iters` blocks in registers, in two independent
+// chains (each block's counter taken from the previous block's output), with the engine's own
+// Philox4x32-10 (precomputed round keys, as the expansion kernels use it); one word per thread is
+// stored so that nothing is optimised away.
+__global__ void __launch_bounds__(256) k_philox_rate(RoundKeys rk, int32_t iters, uint32_t *__restrict__ sink) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    U4 a{t, 0u, 0u, 0u}, b{t, 1u, 0u, 0u};
+    for (int32_t i = 0; i < iters; ++i) {
+        a = philox4x32_10(a.x, a.y ^ (uint32_t)i, a.z, a.w, rk);
+        b = philox4x32_10(b.x, b.y ^ (uint32_t)i, b.z, b.w, rk);
+    }
+    sink[t] = a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
+}
+
 static void free_dev(cnd_graph_dev &d) {
     cudaFree(d.row_ptr);
     cudaFree(d.ic_edge);
     cudaFree(d.lt_edge);
     cudaFree(d.in_row_ptr);
     cudaFree(d.in_edge);
+    cudaFree(d.lt_cnt_edge);
+    cudaFree(d.lt_cnt_off);
+    cudaFree(d.lt_unit_w);
     d = cnd_graph_dev{};
 }
 
@@ -140,6 +169,13 @@ cnd_status cnd_graph_create(int32_t n, int32_t m, const int32_t *row_ptr, const 
             }
         }
     }
+    // LT counting form: possible when, at every node, the in-edges of non-zero weight all carry
+    // the same weight w_v.  Then the active in-weight of v in a trial is k * w_v for k active
+    // in-neighbours over such edges, and k * w_v > theta  <=>  k > floor(theta / w_v): a count
+    // of at most k_v <= 2^L_v - 1 replaces the 32-bit sum.
+    std::vector<int32_t> cnt_off;
+    std::vector<uint32_t> unit_w;
+    int64_t planes = 0;
     if (lt_weight_fx) {
         std::vector<uint64_t> insum((size_t)n, 0);
         for (int32_t e = 0; e < m; ++e) insum[col[e]] += lt_weight_fx[e];
@@ -149,6 +185,32 @@ cnd_status cnd_graph_create(int32_t n, int32_t m, const int32_t *row_ptr, const 
                           (unsigned long long)insum[v]);
                 return CND_EOVERFLOW;
             }
+        unit_w.assign((size_t)n, 0u);
+        std::vector<int64_t> k((size_t)n, 0);
+        bool equal = true;
+        for (int32_t e = 0; e < m && equal; ++e) {
+            const uint32_t x = lt_weight_fx[e];
+            if (x == 0u) continue;
+            const int32_t v = col[e];
+            if (unit_w[v] == 0u) unit_w[v] = x;
+            equal = unit_w[v] == x;
+            k[v]++;
+        }
+        if (equal) {
+            cnt_off.assign((size_t)n + 1, 0);
+            for (int32_t v = 0; v < n; ++v) {
+                int32_t L = 0;
+                while (L < 32 && (k[v] >> L) != 0) ++L;  // bits of k_v: 2^L - 1 >= k_v
+                planes += L;
+                // the edge tag holds the first plane in 27 bits
+                if (planes >= ((int64_t)1 << 27)) break;
+                cnt_off[v + 1] = (int32_t)planes;
+            }
+            if (planes >= ((int64_t)1 << 27)) {
+                cnt_off.clear();
+                planes = 0;
+            }
+        }
     }
     // ---- in-CSR permutation (counting sort by target, stable in edge id)
     std::vector<int32_t> in_row_ptr((size_t)n + 1, 0);
@@ -208,6 +270,15 @@ cnd_status cnd_graph_create(int32_t n, int32_t m, const int32_t *row_ptr, const 
             if ((e = cudaMalloc(&d_w, sizeof(uint32_t) * mb)) != cudaSuccess) { fail(e, "alloc w"); break; }
             if (m > 0 && (e = cudaMemcpy(d_w, lt_weight_fx, sizeof(uint32_t) * (size_t)m, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy w"); break; }
             k_build_lt_edges<<<blocks, threads>>>(m, d_col, d_w, d.lt_edge);
+            if (!cnt_off.empty()) {
+                if ((e = cudaMalloc(&d.lt_cnt_edge, sizeof(uint2) * mb)) != cudaSuccess) { fail(e, "alloc lt_cnt_edge"); break; }
+                if ((e = cudaMalloc(&d.lt_cnt_off, sizeof(int32_t) * ((size_t)n + 1))) != cudaSuccess) { fail(e, "alloc lt_cnt_off"); break; }
+                if ((e = cudaMalloc(&d.lt_unit_w, sizeof(uint32_t) * (size_t)n)) != cudaSuccess) { fail(e, "alloc lt_unit_w"); break; }
+                if ((e = cudaMemcpy(d.lt_cnt_off, cnt_off.data(), sizeof(int32_t) * ((size_t)n + 1), cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy lt_cnt_off"); break; }
+                if ((e = cudaMemcpy(d.lt_unit_w, unit_w.data(), sizeof(uint32_t) * (size_t)n, cudaMemcpyHostToDevice)) != cudaSuccess) { fail(e, "copy lt_unit_w"); break; }
+                k_build_lt_cnt_edges<<<blocks, threads>>>(m, d_col, d_w, d.lt_cnt_off, d.lt_cnt_edge);
+                d.lt_planes = planes;
+            }
         }
         if ((e = cudaMalloc(&d.in_edge, sizeof(uint4) * mb)) != cudaSuccess) { fail(e, "alloc in_edge"); break; }
         if ((e = cudaMalloc(&d_tmp_a, sizeof(int32_t) * mb)) != cudaSuccess) { fail(e, "alloc tmp"); break; }
@@ -286,6 +357,50 @@ cnd_status cnd_philox4x32_10(uint64_t rng_seed, const uint32_t *ctr, int64_t cou
     cudaFree(dc);
     cudaFree(dout);
     return st;
+}
+
+cnd_status cnd_philox_rate(int32_t iters, void *stream, double *blocks_per_s_out, double *ms_out) {
+    clear_error();
+    if (iters <= 0 || !blocks_per_s_out) {
+        set_error("cnd_philox_rate: bad arguments");
+        return CND_EINVAL;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    CND_CUDA_TRY(cudaGetDevice(&dev));
+    CND_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CND_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_philox_rate, 256, 0));
+    const int blocks = sms * std::max(per_sm, 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *sink = nullptr;
+    CND_CUDA_TRY(cudaMalloc(&sink, sizeof(uint32_t) * 256 * (size_t)blocks));
+    const RoundKeys rk = round_keys(0x0123456789ABCDEFull);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cnd_status rs = CND_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess) {
+            set_error("cnd_philox_rate: %s", cudaGetErrorString(e));
+            rs = CND_ECUDA;
+            break;
+        }
+        k_philox_rate<<<blocks, 256, 0, st>>>(rk, std::min(iters, 16), sink);  // warm-up
+        cudaEventRecord(e0, st);
+        k_philox_rate<<<blocks, 256, 0, st>>>(rk, iters, sink);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+            set_error("cnd_philox_rate: %s", cudaGetErrorString(e));
+            rs = CND_ECUDA;
+            break;
+        }
+        *blocks_per_s_out = 2.0 * 256.0 * (double)blocks * (double)iters / (ms * 1e-3);
+        if (ms_out) *ms_out = ms;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    return rs;
 }
 
 }  // extern "C"

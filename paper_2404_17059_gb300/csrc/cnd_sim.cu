@@ -10,6 +10,9 @@
 //                  LT: trials whose accumulator grew in the current step
 //   dmask[v*nq+q]  bit w%64 of word q set <=> nxt[v*B + w] != 0 (nq = ceil(B/64))
 //   acc[(v*B + w)*64 + b]   LT: active in-weight of v in that trial (uint32)
+//   planes[cnt_off[v]*B + w*L_v + i]   LT, counting form (every node's non-zero
+//                  in-weights equal, as in the weighted cascade): bit i of a
+//                  64-lane bit-sliced counter per (node, word), L_v planes
 //
 // Frontier.  In a step, a node is newly active in only some of the pass's
 // trials, and those trials are scattered over its words; the frontier keeps
@@ -27,6 +30,9 @@
 //              or-ed into vis_v and nxt_v; v is listed once per step
 //   LT push    task: for each trial of f & ~vis_v[w], add w(u,v) to acc and
 //              mark the word touched; v is listed once per step
+//              (counting form: one bit-sliced increment of v's counter word by
+//              the trials of f & ~vis_v[w]; a carry out of the top plane is
+//              the activation, see k_lt_init)
 //   finalize   per listed node: IC takes the dirty words of nxt; LT draws the
 //              thresholds of the touched trials and activates where
 //              acc > theta; the non-empty words become the next frontier
@@ -97,6 +103,11 @@ struct Params {
     uint64_t *vis, *nxt, *dmask;
     uint64_t *cvt;             // LT: [v*nq+q] bit w%64 set <=> acc row (v, w) holds ~theta + sum
     uint32_t *acc;
+    // LT counting form (nodes with equal in-weights): bit-sliced counters, plane i of node v
+    // and word w at planes[cnt_off[v] * B + w * L_v + i], L_v = cnt_off[v+1] - cnt_off[v]
+    uint64_t *planes;
+    const int32_t *cnt_off;
+    const uint32_t *unit_w;
     uint32_t *mark;            // [n] last stamp that listed the node
     int32_t *lin, *lin_cnt;    // [n] nodes the current step finalizes (its push lists them here)
     int32_t *lnext, *lnext_cnt;// [n] nodes whose words wait for the next step (deferral)
@@ -501,6 +512,81 @@ __global__ void __launch_bounds__(kBlock, MODE == 2 ? 4 : 6) k_finalize(Params p
     count_add(p, C_DRAWS, n_dr);
 }
 
+// ---------------------------------------------------------------- LT counting form
+// Set-up of a pass in the counting form (every node's non-zero in-weights equal w_v).  With k
+// active in-neighbours, v activates iff k * w_v > theta, i.e. iff k > q = floor(theta / w_v).
+// Each (node, word) keeps one counter per trial, bit-sliced over L_v planes (plane i holds bit i
+// of the 64 trials' counters), started at c0 = 2^L_v - 1 - q (0 when q >= 2^L_v - 1): the k-th
+// increment then carries out of the top plane exactly when k > q.  Since k never exceeds
+// k_v <= 2^L_v - 1, c0 + k < 2^(L_v+1) and the carry happens at most once per trial, so the
+// push can take it as the activation.  One warp per node; each iteration fills two words:
+// lanes 0-15 draw the 64 thresholds of the first (one Philox block of 4 trials per lane),
+// lanes 16-31 those of the second.
+template <bool PERWORD>
+__global__ void __launch_bounds__(kBlock) k_lt_init(Params p) {
+    const int lane = lane_id();
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    const int B = p.B;
+    const int h = lane >> 4, j = lane & 15;
+    uint32_t n_dr = 0;
+    for (int v = warp; v < p.n; v += n_warps) {
+        const int32_t o0 = p.cnt_off[v];
+        const int L = p.cnt_off[v + 1] - o0;
+        if (L == 0) continue;
+        const uint32_t wv = p.unit_w[v];
+        const uint32_t top = (L >= 32) ? 0xFFFFFFFFu : ((1u << L) - 1u);
+        uint64_t *base0 = p.planes + (size_t)o0 * B;
+        for (int w0 = 0; w0 < B; w0 += 2) {
+            // the counter starts of this lane's 4-trial block
+            const int wh = min(w0 + h, B - 1);
+            const U4 th = draw<PERWORD>(p, wh, (uint32_t)v, word_g0<PERWORD>(p, wh) + (uint64_t)j, 1u);
+            if (w0 + h < B) ++n_dr;
+            uint32_t c0[4];
+            const uint32_t tv[4] = {th.x, th.y, th.z, th.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t q = tv[k] / wv;
+                c0[k] = q < top ? top - q : 0u;
+            }
+            // trial t of a word sits in component t & 3 of the block drawn by lane t >> 2 of its
+            // half; this lane gathers trials lane and lane + 32 of both words
+            uint32_t a[4];  // {word 0 trial lane, word 0 trial lane+32, word 1 trial lane, word 1 trial lane+32}
+#pragma unroll
+            for (int q4 = 0; q4 < 4; ++q4) {
+                const int src = 16 * (q4 >> 1) + 8 * (q4 & 1) + (lane >> 2);
+                const uint32_t x0 = __shfl_sync(kFull, c0[0], src), x1 = __shfl_sync(kFull, c0[1], src),
+                               x2 = __shfl_sync(kFull, c0[2], src), x3 = __shfl_sync(kFull, c0[3], src);
+                const int cmp = lane & 3;
+                a[q4] = cmp == 0 ? x0 : cmp == 1 ? x1 : cmp == 2 ? x2 : x3;
+            }
+            // planes of word w0 then of w0 + 1 are one contiguous run of 2L words: element e of
+            // the run is kept by lane e % 32 in slot e / 32
+            uint64_t s0 = 0, s1 = 0;
+            for (int i = 0; i < L; ++i) {
+                const uint64_t P0 = (uint64_t)__ballot_sync(kFull, (a[0] >> i) & 1u) |
+                                    ((uint64_t)__ballot_sync(kFull, (a[1] >> i) & 1u) << 32);
+                const uint64_t P1 = (uint64_t)__ballot_sync(kFull, (a[2] >> i) & 1u) |
+                                    ((uint64_t)__ballot_sync(kFull, (a[3] >> i) & 1u) << 32);
+                const int e0 = i, e1 = L + i;
+                if ((e0 & 31) == lane) {
+                    if (e0 < 32) s0 = P0;
+                    else s1 = P0;
+                }
+                if ((e1 & 31) == lane) {
+                    if (e1 < 32) s0 = P1;
+                    else s1 = P1;
+                }
+            }
+            const int run = (w0 + 1 < B) ? 2 * L : L;
+            uint64_t *out = base0 + (size_t)w0 * L;
+            if (lane < run) out[lane] = s0;
+            if (32 + lane < run) out[32 + lane] = s1;
+        }
+    }
+    count_add(p, C_DRAWS, n_dr);
+}
+
 // ---------------------------------------------------------------- push
 // One warp per work item: the item's (edge, pair) tasks are spread over the
 // lanes, task t = (edge t / k, pair t % k).
@@ -591,6 +677,31 @@ __global__ void __launch_bounds__(kBlock, kPushMinBlocks) k_push(Params p_) {
                     if (ic_thr != 0u) {
                         ++n_wc;
                         ic_c = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
+                    }
+                } else if (MODEL == 2) {
+                    // counting form: add 1 to the counters of the trials of c (bit-sliced ripple
+                    // carry, plane by plane, atomically); what carries out of the top plane
+                    // activates (see k_lt_init)
+                    const uint32_t tag = ed.y;
+                    if (tag != 0u) {
+                        ++n_wc;
+                        uint64_t carry = f & ~(uint64_t)__ldcg((const unsigned long long *)p.vis + idx);
+                        if (carry) {
+                            const uint32_t L = tag & 31u;
+                            unsigned long long *pl =
+                                (unsigned long long *)p.planes + ((size_t)(tag >> 5) * B + (size_t)w * L);
+                            for (uint32_t i = 0; i < L && carry; ++i) {
+                                ++n_up;
+                                carry &= (uint64_t)atomicXor(pl + i, (unsigned long long)carry);
+                            }
+                            if (carry) {
+                                atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)carry);
+                                const uint64_t old =
+                                    atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)carry);
+                                mark_dirty(p, v, w, old);
+                                hit = true;
+                            }
+                        }
                     }
                 } else {
                     const uint32_t wt = ed.y;
@@ -702,13 +813,13 @@ __global__ void __launch_bounds__(kBlock, kPushMinBlocks) k_push(Params p_) {
                     }
                 }
                 if (nb) {
-                    nb &= ~(uint64_t)atomicOr((unsigned long long *)p.vis + ic_idx, (unsigned long long)nb);
-                    if (nb) {
-                        const uint64_t old = atomicOr((unsigned long long *)p.nxt + ic_idx, (unsigned long long)nb);
-                        mark_dirty(p, ic_v, ic_w, old);
-                        ++n_up;
-                        hit = true;
-                    }
+                    // vis: a reduction without return (no round trip); bits another task of this
+                    // step has just set are or-ed again into nxt, which is idempotent
+                    atomicOr((unsigned long long *)p.vis + ic_idx, (unsigned long long)nb);
+                    const uint64_t old = atomicOr((unsigned long long *)p.nxt + ic_idx, (unsigned long long)nb);
+                    mark_dirty(p, ic_v, ic_w, old);
+                    ++n_up;
+                    hit = true;
                 }
                 __syncwarp();
             }
@@ -1056,7 +1167,9 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
                             const cnd_sim_opts &o, Work &W, bool &limit_hit) {
     cudaStream_t st = W.st;
     const int32_t n = G.n;
-    const uint2 *edge = model == 0 ? G.ic_edge : G.lt_edge;
+    // LT in the counting form where the graph allows it (unless the caller asks for the sums)
+    const bool lt_cnt = model == 1 && G.lt_cnt_edge != nullptr && !o.lt_accumulate;
+    const uint2 *edge = model == 0 ? G.ic_edge : (lt_cnt ? G.lt_cnt_edge : G.lt_edge);
     int64_t total_words = 0;
     for (const auto &it : items) total_words += (it.trials + 63) / 64;
     cnd_sim_stats *S = o.stats;
@@ -1068,7 +1181,7 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
         CND_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, sizeof(unsigned long long) * C_N, st));
     }
     struct Events {
-        cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+        cudaEvent_t e[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
         ~Events() {
             for (auto x : e)
                 if (x) cudaEventDestroy(x);
@@ -1076,8 +1189,14 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     } ev;
     if (timing)
         for (auto &x : ev.e) CND_CUDA_TRY(cudaEventCreate(&x));
-    bool timing_pending = false;
+    bool timing_pending = false, setup_pending = false;
     auto collect_timing = [&]() -> cnd_status {
+        if (setup_pending) {
+            float c = 0.f;
+            CND_CUDA_TRY(cudaEventElapsedTime(&c, ev.e[4], ev.e[5]));
+            S->setup_ms += c;
+            setup_pending = false;
+        }
         if (!timing_pending) return CND_OK;
         float a = 0.f, b = 0.f;
         CND_CUDA_TRY(cudaEventElapsedTime(&a, ev.e[0], ev.e[1]));
@@ -1092,8 +1211,9 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     size_t free_b = 0, total_b = 0;
     CND_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     const double budget = 0.6 * (double)free_b;
-    // bytes per word column: vis, nxt, two pair pools (+ LT accumulators)
-    const double per_word = (double)n * (2 * 8 + 2 * 10 + (model == 1 ? 256 : 0));
+    // bytes per word column: vis, nxt, two pair pools (+ LT accumulators or counter planes)
+    const double per_word = (double)n * (2 * 8 + 2 * 10 + (model == 1 && !lt_cnt ? 256 : 0)) +
+                            (lt_cnt ? 8.0 * (double)G.lt_planes : 0.0);
     // pulling (IC) happens only when asked for: by direction, or by a switch threshold
     const bool may_pull = model == 0 && G.m > 0 &&
                           (o.direction == CND_DIR_PULL || (o.direction == CND_DIR_AUTO && o.pull_permille > 0));
@@ -1221,7 +1341,11 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     P.tau = o.defer_bits;
     P.max_wait = o.defer_steps;
     if (o.defer_bits > 0 && o.defer_steps > 0) CND_CUDA_TRY(W.alloc(&P.age, nB));
-    if (model == 1) {
+    if (lt_cnt) {
+        CND_CUDA_TRY(W.alloc(&P.planes, (size_t)G.lt_planes * (size_t)B));
+        P.cnt_off = G.lt_cnt_off;
+        P.unit_w = G.lt_unit_w;
+    } else if (model == 1) {
         CND_CUDA_TRY(W.alloc(&P.acc, nB * 64));
         CND_CUDA_TRY(W.alloc(&P.cvt, (size_t)n * nq));
     }
@@ -1248,6 +1372,7 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     if (S) {
         S->passes = (int32_t)passes.size();
         S->word_bits = 64 * B;
+        S->lt_counters = lt_cnt ? 1 : 0;
     }
     CND_CUDA_TRY(cudaMemsetAsync(P.mark, 0xFF, sizeof(uint32_t) * (size_t)n, st));
     CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
@@ -1256,10 +1381,17 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     int32_t *hcnt = t_pinned.h;
 
     // a pass whose columns share one key takes it as launch parameters
-    const void *k_push_pw = model == 0 ? push_fn<0, true>() : push_fn<1, true>();
-    const void *k_push_uk = model == 0 ? push_fn<0, false>() : push_fn<1, false>();
-    const void *k_fin_pw = model == 0 ? (const void *)k_finalize<1, true> : (const void *)k_finalize<2, true>;
-    const void *k_fin_uk = model == 0 ? (const void *)k_finalize<1, false> : (const void *)k_finalize<2, false>;
+    // (the counting form's push draws nothing and its finalize only collects, like IC's)
+    const void *k_push_pw = model == 0 ? push_fn<0, true>() : lt_cnt ? push_fn<2, false>() : push_fn<1, true>();
+    const void *k_push_uk = model == 0 ? push_fn<0, false>() : lt_cnt ? push_fn<2, false>() : push_fn<1, false>();
+    const void *k_fin_pw = model == 0 ? (const void *)k_finalize<1, true>
+                           : lt_cnt   ? (const void *)k_finalize<1, false>
+                                      : (const void *)k_finalize<2, true>;
+    const void *k_fin_uk = model == 0 ? (const void *)k_finalize<1, false>
+                           : lt_cnt   ? (const void *)k_finalize<1, false>
+                                      : (const void *)k_finalize<2, false>;
+    const void *k_init_pw = (const void *)k_lt_init<true>, *k_init_uk = (const void *)k_lt_init<false>;
+    const int init_blocks = G.num_sms * resident_blocks(k_init_uk);
     const void *k_seedfin = (const void *)k_finalize<1, false>;
     const int push_blocks = G.num_sms * resident_blocks(k_push_uk);
     const void *k_pull_pw = (const void *)k_pull_ic<true>, *k_pull_uk = (const void *)k_pull_ic<false>;
@@ -1280,11 +1412,19 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
         const int64_t *d_wout = pass_wout(pass);
         const int32_t *d_witem = pass_witem(pass);
         const SeedSeg *d_segs = pass_segs(pass);
+        if (timing) CND_CUDA_TRY(cudaEventRecord(ev.e[4], st));
         CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, st));
         if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, st));
-        if (model == 1) {
+        if (lt_cnt) {
+            CND_CUDA_TRY(launch(pw ? k_init_pw : k_init_uk, init_blocks, st, P));
+            launches += 1;
+        } else if (model == 1) {
             CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, st));
             CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, st));
+        }
+        if (timing) {
+            CND_CUDA_TRY(cudaEventRecord(ev.e[5], st));
+            setup_pending = true;
         }
         const void *k_push_fn = pw ? k_push_pw : k_push_uk;
         const void *k_fin_fn = pw ? k_fin_pw : k_fin_uk;
@@ -1444,7 +1584,10 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
             CND_CUDA_TRY(cap_begin(gr.g, tail));
             CND_CUDA_TRY(cudaMemsetAsync(P.vis, 0, sizeof(uint64_t) * nB, cs));
             if (P.age) CND_CUDA_TRY(cudaMemsetAsync(P.age, 0, nB, cs));
-            if (model == 1) {
+            if (lt_cnt) {
+                CND_CUDA_TRY(launch(pw ? k_init_pw : k_init_uk, init_blocks, cs, Q));
+                launches += 1;
+            } else if (model == 1) {
                 CND_CUDA_TRY(cudaMemsetAsync(P.acc, 0, sizeof(uint32_t) * nB * 64, cs));
                 CND_CUDA_TRY(cudaMemsetAsync(P.cvt, 0, sizeof(uint64_t) * (size_t)n * nq, cs));
             }
@@ -1688,7 +1831,7 @@ static cnd_status simulate_common(int model, const cnd_graph *g, const char *fn,
         (o.first_trial & 63) || o.word_bits < 0 || (o.word_bits & 63) || o.word_bits > 64 * kMaxB ||
         o.level_counts_len < 0 || (o.level_counts_len > 0 && !o.level_counts_out) || o.chunk_edges < 0 ||
         o.direction < 0 || o.direction > 2 || o.defer_bits < 0 || o.defer_bits > 64 || o.defer_steps < 0 ||
-        o.defer_steps > 255) {
+        o.defer_steps > 255 || o.lt_accumulate < 0 || o.lt_accumulate > 1) {
         set_error("%s: bad arguments (items, first_trial %% 64, word_bits, level_counts, chunk, defer)", fn);
         return CND_EINVAL;
     }

@@ -27,7 +27,7 @@ __all__ = [
     "Graph", "csr_from_edges", "erdos_renyi_m", "barabasi_albert", "rmat",
     "random_regular", "watts_strogatz", "path_graph", "out_star", "in_star",
     "ic_uniform", "ic_weighted_cascade", "ic_uniform_random", "ic_trivalency",
-    "lt_weighted_cascade", "top_degree_seeds", "uniform_seeds", "batch_items",
+    "lt_weighted_cascade", "lt_random", "top_degree_seeds", "uniform_seeds", "batch_items",
     "save_csr", "load_csr", "read_edge_list",
 ]
 
@@ -397,6 +397,17 @@ def lt_weighted_cascade(g: Graph) -> np.ndarray:
     nz = indeg > 0
     w[nz] = np.uint64(LT_ONE) // indeg[nz].astype(np.uint64)
     return w[g.col].astype(np.uint32)
+
+
+def lt_random(g: Graph, total: float = 1.0, graph_seed: int = 1) -> np.ndarray:
+    """LT weights that differ between a node's in-edges: raw U[0.1, 1) per edge, scaled so that each
+    node's in-weights sum to at most total * (2^32-1) (floored, uint32)."""
+    rng = _rng(graph_seed + 0x17EED)
+    raw = rng.uniform(0.1, 1.0, size=g.m)
+    tot = np.zeros(g.n)
+    np.add.at(tot, g.col, raw)
+    w = np.floor(raw / tot[g.col] * (float(total) * LT_ONE)).astype(np.uint64)
+    return np.minimum(w, LT_ONE).astype(np.uint32)
 
 
 # ---------------------------------------------------------------- seed sets

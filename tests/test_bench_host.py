@@ -1,5 +1,5 @@
 """Host logic of bench.py: the algorithmic-byte count of the expansion kernels, the traffic lookup keyed
-by the engine sources, model selection and the derived integer-multiply peak (no GPU needed)."""
+by the engine sources, model selection and the rotation of trial ranges over steps (no GPU needed)."""
 import json
 import os
 import sys
@@ -21,12 +21,30 @@ def test_alg_bytes_per_term():
     s = dict(base, work_items=0, updates=1)
     assert bench.alg_bytes("ic", s) == 16   # vis and nxt read-modify-write
     assert bench.alg_bytes("lt", s) == 8    # one 4-byte accumulator read and write
+    assert bench.alg_bytes("lt", dict(s, lt_counters=1)) == 16  # one 8-byte counter plane read and write
 
 
-def test_philox_peak_from_unit_counts():
-    # 152 SMs x 64 multiplies per clock x 2.07 GHz, 40 multiply results per Philox-4x32-10 call
-    assert bench.PHILOX_PEAK_G == pytest.approx(152 * 64 * 2.07 / 40)
-    assert 500 < bench.PHILOX_PEAK_G < 510
+def test_kernel_names():
+    assert bench.kernel_name("ic", {}) == "k_push<0>"
+    assert bench.kernel_name("lt", {"lt_counters": 0}) == "k_push<1>"
+    assert bench.kernel_name("lt", {"lt_counters": 1}) == "k_push<2>"
+
+
+def test_trial_ranges_rotate_through_the_configuration():
+    wl = bench.Workload("x", "", None, {"ic": 1, "lt": 1}, trials={"ic": 2048, "lt": 1000}, total=100_000)
+    k_ic = 100_000 // 2048
+    firsts = [wl.first_trial("ic", s, 0, 1) for s in range(2 * k_ic)]
+    assert firsts[:k_ic] == [2048 * i for i in range(k_ic)] and firsts[k_ic:] == firsts[:k_ic]
+    assert all(f + 2048 <= 100_000 for f in firsts)
+    # LT ranges are 64-aligned (1000 trials span 1024 ids) and stay inside the configuration too
+    lt = [wl.first_trial("lt", s, 0, 1) for s in range(200)]
+    assert all(f % 64 == 0 and f + 1000 <= 100_000 for f in lt) and len(set(lt)) == 100_000 // 1024
+    # ranks take disjoint ranges within a step
+    assert len({wl.first_trial("ic", 3, r, 4) for r in range(4)}) == 4
+    # a workload whose steps cover the whole configuration: every step the same ids, ranks their own
+    whole = bench.Workload("y", "", None, {"ic": 1}, trials={"ic": 1000}, total=1000)
+    assert [whole.first_trial("ic", s, 0, 1) for s in range(3)] == [0, 0, 0]
+    assert whole.first_trial("ic", 0, 2, 4) == 2 * 1024
 
 
 def test_traffic_lookup_needs_the_current_sources(tmp_path, monkeypatch):
@@ -47,10 +65,10 @@ def test_traffic_lookup_needs_the_current_sources(tmp_path, monkeypatch):
 
 
 def test_committed_traffic_matches_the_engine():
-    """The committed traffic figures were taken on the current engine sources."""
-    assert bench.ncu_traffic("k_push<1>", "ba100k", 1.0) is not None
-    assert bench.ncu_traffic("k_push<0>", "ba100k", 1.0) is not None
-    assert bench.ncu_traffic("k_push<0>", "rmat24", 1.0) is not None
+    """The committed traffic figures of the default workload's expansion kernels were taken on the current
+    engine sources (a smaller R-MAT of the same generator, scale 21, keeps the capture small)."""
+    assert bench.ncu_traffic("k_push<0>", "rmat21", 1.0) is not None
+    assert bench.ncu_traffic("k_push<2>", "rmat21", 1.0) is not None
 
 
 def test_select_models():

@@ -36,6 +36,29 @@ def test_noalloc_matches_regular_entry_point_twice():
         assert np.array_equal(counts.cpu().numpy(), ref.node_count)
 
 
+def test_noalloc_several_passes_match_regular_entry_point():
+    """A graph large enough that the scratch holds only some words per pass (BA n=100,000: about a dozen
+    64-trial words), so a call runs several passes: the per-pass re-upload of the word descriptors, the
+    per-pass clear of the active sets, stamps that continue across passes and node counts summed over
+    passes are all exercised; two calls in a row, the second with a ragged last word."""
+    torch = pytest.importorskip("torch")
+    g = I.barabasi_albert(100_000, 5, graph_seed=1)
+    p = I.ic_weighted_cascade(g)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    seeds = I.top_degree_seeds(g, 50)
+    for T, rng in ((4096, 3), (2500, 4)):
+        s = torch.as_tensor(seeds, dtype=torch.int32, device=dev)
+        spread = torch.full((T,), -7, dtype=torch.int32, device=dev)
+        counts = torch.full((g.n,), -7, dtype=torch.int32, device=dev)
+        assert P.cnd_ic_simulate_noalloc(G, s, T, rng, spread, counts) == P.CND_OK
+        torch.cuda.synchronize()
+        ref = P.cnd_ic_simulate_ex(G, seeds, T, rng, stats=P.CND_STATS_COUNT)
+        assert ref.stats["passes"] == 1  # the regular call holds all its words in one pass
+        assert np.array_equal(spread.cpu().numpy(), ref.spread)
+        assert np.array_equal(counts.cpu().numpy(), ref.node_count)
+
+
 def test_noalloc_rejects_graph_beyond_scratch():
     torch = pytest.importorskip("torch")
     g = I.rmat(20, 1 << 22, graph_seed=5)
