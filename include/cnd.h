@@ -108,6 +108,10 @@ typedef struct cnd_sim_stats {
     int32_t pad0;
     double setup_ms;           /* CUDA-event time of the per-pass set-up: state zero fills and, in
                                   the counting form, the counter start values (CND_STATS_TIMING) */
+    int32_t graph_reused;      /* graph mode: 1 if the call updated an executable graph cached by an
+                                  earlier call of the same shape on this host thread, 0 if it
+                                  instantiated one */
+    int32_t pad1;
 } cnd_sim_stats;
 
 /* Options of the *_ex entry points.  Zero-initialise (cnd_sim_opts_init). */
@@ -145,7 +149,9 @@ typedef struct cnd_sim_opts {
     int32_t graph;             /* 1: run the whole call as one CUDA graph launch -- every pass
                                   and its step loop (a device-side WHILE node whose condition a
                                   one-thread control kernel sets after each step), no host round
-                                  trip per step; ignored with CND_STATS_TIMING */
+                                  trip per step; ignored with CND_STATS_TIMING.  Each host thread
+                                  keeps the executable graphs of its recent call shapes (up to 16)
+                                  and updates a matching one in place rather than instantiating */
     int32_t autotune;          /* 1: take word_bits, chunk_edges, pull_permille and graph from the
                                   autotuner's cache for this graph, model and problem size class,
                                   tuning (cnd_autotune on a sample of this call) on a miss */

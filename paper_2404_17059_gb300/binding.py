@@ -64,6 +64,8 @@ class cnd_sim_stats(C.Structure):
         ("lt_counters", C.c_int32),
         ("pad0", C.c_int32),
         ("setup_ms", C.c_double),
+        ("graph_reused", C.c_int32),
+        ("pad1", C.c_int32),
     ]
 
     def as_dict(self):

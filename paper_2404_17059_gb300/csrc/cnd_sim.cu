@@ -1091,6 +1091,34 @@ static int resident_blocks(const void *fn) {
 }
 
 // ---------------------------------------------------------------- driver
+// Instantiated call graphs of recent call shapes, per host thread.  Every graph-mode call captures
+// its graph (cheap: API calls only); when a cached executable of the same shape exists it is
+// updated in place with the new capture's parameters (cudaGraphExecUpdate) instead of a new
+// instantiation.  The capture stream is kept too.  Per thread, so that two host threads never
+// share an executable; a call waits for its launch to finish before it returns, so the next call
+// of the thread may update it.
+struct ExecCache {
+    struct Entry {
+        uint64_t key;
+        int device;
+        cudaGraphExec_t x;
+    };
+    std::vector<Entry> e;
+    cudaStream_t cs = nullptr;
+    int cs_device = -1;
+    ~ExecCache() {
+        for (auto &q : e) cudaGraphExecDestroy(q.x);
+        if (cs) cudaStreamDestroy(cs);
+    }
+};
+static thread_local ExecCache t_exec;
+constexpr size_t kExecCacheSize = 16;
+
+static uint64_t mix_key(uint64_t h, uint64_t v) {
+    h ^= v + 0x9E3779B97F4A7C15ull + (h << 6) + (h >> 2);
+    return h;
+}
+
 struct Work {
     cudaStream_t st = nullptr;
     std::vector<void *> allocs;
@@ -1544,17 +1572,28 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
         P.lcnt = d_lcnt;
         struct Graph {
             cudaGraph_t g = nullptr;
-            cudaGraphExec_t x = nullptr;
-            cudaStream_t cs = nullptr;
             ~Graph() {
-                if (x) cudaGraphExecDestroy(x);
                 if (g) cudaGraphDestroy(g);
-                if (cs) cudaStreamDestroy(cs);
             }
         } gr;
-        CND_CUDA_TRY(cudaStreamCreateWithFlags(&gr.cs, cudaStreamNonBlocking));
+        if (!t_exec.cs || t_exec.cs_device != G.device) {
+            if (t_exec.cs) cudaStreamDestroy(t_exec.cs);
+            t_exec.cs = nullptr;
+            CND_CUDA_TRY(cudaStreamCreateWithFlags(&t_exec.cs, cudaStreamNonBlocking));
+            t_exec.cs_device = G.device;
+        }
         CND_CUDA_TRY(cudaGraphCreate(&gr.g, 0));
-        cudaStream_t cs = gr.cs;
+        cudaStream_t cs = t_exec.cs;
+        // shape of the call graph: what decides its nodes and their kinds (launch dimensions and
+        // parameters may differ between calls of one shape)
+        uint64_t shape = mix_key(0, (uint64_t)model);
+        shape = mix_key(shape, lt_cnt ? 1 : 0);
+        shape = mix_key(shape, (uint64_t)passes.size());
+        shape = mix_key(shape, may_pull ? 1 : 0);
+        shape = mix_key(shape, P.age ? 1 : 0);
+        shape = mix_key(shape, (uint64_t)B);
+        shape = mix_key(shape, (uint64_t)n);
+        for (size_t pass = 0; pass < passes.size(); ++pass) shape = mix_key(shape, pinfo[pass].perword ? 1 : 0);
         std::vector<cudaGraphNode_t> tail;
         auto cap_begin = [&](cudaGraph_t target, const std::vector<cudaGraphNode_t> &deps) -> cudaError_t {
             return cudaStreamBeginCaptureToGraph(cs, target, deps.empty() ? nullptr : deps.data(), nullptr, deps.size(),
@@ -1635,8 +1674,30 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
             CND_CUDA_TRY(cap_end(&tail));
             launches += 6;
         }
-        CND_CUDA_TRY(cudaGraphInstantiate(&gr.x, gr.g, 0));
-        CND_CUDA_TRY(cudaGraphLaunch(gr.x, st));
+        cudaGraphExec_t gx = nullptr;
+        size_t slot = t_exec.e.size();
+        for (size_t i = 0; i < t_exec.e.size(); ++i)
+            if (t_exec.e[i].key == shape && t_exec.e[i].device == G.device) slot = i;
+        if (slot < t_exec.e.size()) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(t_exec.e[slot].x, gr.g, &info) == cudaSuccess) {
+                gx = t_exec.e[slot].x;
+                if (S) S->graph_reused = 1;
+            } else {
+                cudaGetLastError();  // a refused update is not an error of the call
+                cudaGraphExecDestroy(t_exec.e[slot].x);
+                t_exec.e.erase(t_exec.e.begin() + (ptrdiff_t)slot);
+            }
+        }
+        if (!gx) {
+            CND_CUDA_TRY(cudaGraphInstantiate(&gx, gr.g, 0));
+            if (t_exec.e.size() >= kExecCacheSize) {
+                cudaGraphExecDestroy(t_exec.e.front().x);
+                t_exec.e.erase(t_exec.e.begin());
+            }
+            t_exec.e.push_back(ExecCache::Entry{shape, G.device, gx});
+        }
+        CND_CUDA_TRY(cudaGraphLaunch(gx, st));
         Ctl hc;
         CND_CUDA_TRY(cudaMemcpyAsync(&hc, d_ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st));
         CND_CUDA_TRY(cudaStreamSynchronize(st));
