@@ -7,9 +7,9 @@ ingest happens once, before the timed region):
   rmat24 (default)  the large configuration: R-MAT scale 24, edge factor 16 (2^28
                     samples, deduplicated: 263,430,501 edges); IC with p = 0.01
                     and LT with weighted-cascade weights; 100 highest-degree
-                    seeds; 100,000 trials per model.  A step is one IC call on
-                    2,048 trials and one LT call on 1,024 trials (--trials,
-                    --lt-trials), each a contiguous range of trial ids; the
+                    seeds; 100,000 trials per model.  A step is one IC call and
+                    one LT call on 1,024 trials each (--trials, --lt-trials),
+                    each a contiguous range of trial ids; the
                     ranges rotate through the 100,000 from step to step
                     (first_trial), so every step does full trials and no work
                     is skipped.  --scale changes the scale (ncu captures).
@@ -161,7 +161,7 @@ def select_models(wl: Workload, models: str) -> Workload:
     return wl
 
 
-RMAT24_TRIALS = {"ic": 2048, "lt": 1024}  # trials per model per step of the R-MAT workload (of 100,000)
+RMAT24_TRIALS = {"ic": 1024, "lt": 1024}  # trials per model per step of the R-MAT workload (of 100,000)
 
 
 def make_workload(name: str, trials: int = 0, items: int = 0, lt_trials: int = 0, scale: int = 24) -> Workload:
@@ -492,7 +492,8 @@ def run_surrogate(args):
            "frac_of_hbm": fwd_bytes / fwd_s / 1e9 / peak,
            "note": "host wall time of cnd_sur_forward (seed upload and result copy included)"}
     t0 = time.perf_counter()
-    tr = P.cnd_sur_train(sur, args.pairs, n_trials=T, batch_sets=16, sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1)
+    tr = P.cnd_sur_train(sur, args.pairs, n_trials=T, batch_sets=16, sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1,
+                         hub_frac=args.hub_frac)
     train_s = time.perf_counter() - t0
     q1 = quality(sur)
     print(f"trained {args.pairs} pairs in {train_s:.1f} s; held-out before {q0} after {q1}", file=sys.stderr,
@@ -510,11 +511,11 @@ def run_surrogate(args):
                        "edge_checks": rc.edge_checks}
     print(f"mc_celf: {runs['mc_celf']['s']:.2f} s", file=sys.stderr, flush=True)
     variants = (("screened_trained", sur, args.screen_mode), ("screened_trained_onehop_no_rerank", sur, "onehop"),
-                ("screened_trained_gradient", sur, "gradient"),
+                ("screened_trained_gradient", sur, "gradient"), ("screened_trained_mixed", sur, "mixed"),
                 ("screened_trained_onehop", sur, "onehop"), ("screened_untrained", untrained, args.screen_mode),
                 ("screened_degree_no_network", None, "degree"))
     for name, model, mode in variants:
-        no_rerank = name.endswith("no_rerank")
+        no_rerank = name.endswith("no_rerank") or mode in ("mixed", "degree")
         if name != "screened_trained" and not no_rerank and mode == args.screen_mode and model is sur:
             continue
         t0 = time.perf_counter()
@@ -531,6 +532,7 @@ def run_surrogate(args):
             continue
         runs[name]["spread_vs_celf"] = runs[name]["scored_spread"] / base["scored_spread"]
         runs[name]["speedup_vs_celf"] = base["s"] / runs[name]["s"]
+    hubs = surrogate_hubs(P)
     line = {"metric": "surrogate vs MC greedy speedup", "value": runs["screened_trained"]["speedup_vs_celf"],
             "unit": "x", "n_gpus": 1, "steps": 1, "warmup": 0, "ms_per_step": 1e3 * runs["screened_trained"]["s"],
             "higher_is_better": True, "scaling": "replicas only", "vs_baseline": None, "dtype": "bf16+u64",
@@ -545,9 +547,42 @@ def run_surrogate(args):
             "training": {"pairs": args.pairs, "s": train_s, "sim_ms": tr["sim_ms"], "train_ms": tr["train_ms"],
                          "loss_first": float(tr["loss"][:8].mean()), "loss_last": float(tr["loss"][-8:].mean())},
             "speedup_including_training": base["s"] / (runs["screened_trained"]["s"] + train_s),
-            "heldout_untrained": q0, "heldout_trained": q1, "forward": fwd, "runs": runs}
+            "heldout_untrained": q0, "heldout_trained": q1, "forward": fwd, "runs": runs, "overlapping_hubs": hubs}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def surrogate_hubs(P):
+    """The screen on a graph whose highest-degree nodes reach the same nodes (inputs.overlapping_hubs): greedy
+    k=8 with 2 (mixed) or 4 (gradient) simulated candidates per round, trained on hub-including seed sets vs
+    the untrained network vs out-degree (no network) vs MC CELF; spreads scored with 4,096 exact trials."""
+    g = I.overlapping_hubs(graph_seed=1)
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, I.hub_probabilities(g), None)
+    init = I.surrogate_init(1)
+
+    def scored(seeds):
+        r = P.cnd_ic_simulate_ex(G, np.asarray(seeds, dtype=np.int32), 4096, 99, node_count=False)
+        return float(r.spread.astype(np.float64).mean())
+
+    K, T = 8, 512
+    t0 = time.perf_counter()
+    celf = P.cnd_ic_im_celf(G, K, T, 1)
+    out = {"celf": {"spread": scored(celf.seeds), "evaluations": celf.evaluations, "s": time.perf_counter() - t0,
+                    "seeds": celf.seeds.tolist()}}
+    trained = P.cnd_sur_create(G, init)
+    t0 = time.perf_counter()
+    P.cnd_sur_train(trained, 32768, set_size=(1, 20), n_trials=256, batch_sets=16, lr=3e-3, hub_frac=0.5)
+    out["train_s"] = time.perf_counter() - t0
+    for nex, mode in ((2, "mixed"), (4, "gradient")):
+        for name, model, md in (("trained", trained, mode), ("untrained", P.cnd_sur_create(G, init), mode),
+                                ("degree_no_network", None, "degree")):
+            t0 = time.perf_counter()
+            r, _ = P.cnd_ic_im_screened(G, model, K, T, 1, n_screen=nex, n_exact=nex, mode=md)
+            sp = scored(r.seeds)
+            out[f"{name}_{md}_{nex}"] = {"spread": sp, "vs_celf": sp / out["celf"]["spread"],
+                                         "evaluations": r.evaluations, "s": time.perf_counter() - t0,
+                                         "seeds": r.seeds.tolist()}
+    return out
 
 
 def run_table1(args):
@@ -909,8 +944,10 @@ def main():
     ap.add_argument("--k", type=int, default=50, help="surrogate: seeds to choose")
     ap.add_argument("--screen", type=int, default=64, help="surrogate: candidates kept by the gradient score")
     ap.add_argument("--exact", type=int, default=8, help="surrogate: candidates simulated per round")
-    ap.add_argument("--screen-mode", default="onehop", choices=["gradient", "onehop"],
+    ap.add_argument("--screen-mode", default="mixed", choices=["gradient", "onehop", "mixed"],
                     help="surrogate: first score of the screen")
+    ap.add_argument("--hub-frac", type=float, default=0.5,
+                    help="surrogate: share of each training set's seeds drawn in proportion to out-degree")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--trials", type=int, default=0, help="override the workload's (IC) trials per step")
     ap.add_argument("--lt-trials", type=int, default=0, help="override the workload's LT trials per step")

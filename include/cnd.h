@@ -377,8 +377,9 @@ cnd_status cnd_sur_onehop(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, flo
 
 /*
  * Training on pairs the simulator generates on the fly: pair i is a seed set
- * of size U{set_size_lo..set_size_hi} of distinct uniform nodes (drawn from a
- * splitmix64 stream of data_seed and i), with targets y_v = (trials in which
+ * of size U{set_size_lo..set_size_hi} of distinct nodes (uniform, or with
+ * hub_frac partly in proportion to out-degree; drawn from a splitmix64 stream of
+ * data_seed and i), with targets y_v = (trials in which
  * v ends active) / n_trials from n_trials exact IC trials under key
  * rng_seed + i (cnd_ic_simulate_batch).  Adam steps on the mean loss of
  * batch_sets pairs; pairs first_pair .. first_pair + n_pairs - 1.
@@ -398,7 +399,12 @@ typedef struct {
     void *stream;
     double *sim_ms_out;   /* NULL or time spent in the simulator, ms */
     double *train_ms_out; /* NULL or time spent in forward / backward / Adam, ms */
-    int64_t reserved[4];
+    float hub_frac;       /* 0 (default): seeds uniform over the nodes; in (0, 1]: each seed is, with
+                             this probability, the source of a uniform random edge instead (drawn in
+                             proportion to out-degree), so that training sets contain hubs the way
+                             the sets a greedy seed selection scores do (its earlier picks) */
+    int32_t pad;
+    int64_t reserved[3];
 } cnd_sur_train_opts;
 
 void cnd_sur_train_opts_init(cnd_sur_train_opts *o);
@@ -413,6 +419,9 @@ cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, double *loss_o
  *      prediction yhat = yhat(S) (one forward pass),
  *        (1 - yhat_c) (1 + sum over out-edges (c -> w) of q_e (1 - yhat_w));
  *      mode 2: out-degree (no network: the screen without the surrogate);
+ *      mode 3: the n_exact candidates are taken alternately from the best
+ *      by the mode-0 score and the best by out-degree (repeats skipped;
+ *      n_screen unused): the network proposes half of what is simulated;
  *   2. if n_screen > n_exact, re-rank those by the surrogate's predicted
  *      spread of S + c (one forward each) and keep the n_exact best (mode 2
  *      keeps the n_exact best by out-degree directly; s may then be NULL);
@@ -428,7 +437,8 @@ cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, double *loss_o
 typedef struct {
     int32_t n_screen;     /* candidates kept by the first score, >= n_exact (0 = n_exact) */
     int32_t n_exact;      /* candidates simulated per round, >= 1 */
-    int32_t mode;         /* first score: 0 gradient, 1 one-hop gain, 2 out-degree */
+    int32_t mode;         /* first score: 0 gradient, 1 one-hop gain, 2 out-degree, 3 gradient and
+                             out-degree alternately */
     int32_t pad;
     double *sur_ms_out;   /* NULL or wall time in the surrogate, ms */
     double *sim_ms_out;   /* NULL or wall time in the simulator, ms */

@@ -114,7 +114,7 @@ class cnd_sur_train_opts(C.Structure):
         ("first_pair", C.c_int64), ("n_pairs", C.c_int64), ("set_size_lo", C.c_int32), ("set_size_hi", C.c_int32),
         ("n_trials", C.c_int32), ("batch_sets", C.c_int32), ("sim_chunk", C.c_int32), ("lr", C.c_float),
         ("data_seed", C.c_uint64), ("rng_seed", C.c_uint64), ("stream", C.c_void_p), ("sim_ms_out", C.c_void_p),
-        ("train_ms_out", C.c_void_p), ("reserved", C.c_int64 * 4),
+        ("train_ms_out", C.c_void_p), ("hub_frac", C.c_float), ("pad", C.c_int32), ("reserved", C.c_int64 * 3),
     ]
 
 
@@ -639,7 +639,7 @@ def cnd_sur_onehop(s: CndSur, seeds) -> np.ndarray:
 
 
 def cnd_sur_train(s: CndSur, n_pairs, *, first_pair=0, set_size=(1, 50), n_trials=1024, batch_sets=16,
-                  sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1, stream=None) -> dict:
+                  sim_chunk=256, lr=1e-3, data_seed=1, rng_seed=1, stream=None, hub_frac=0.0) -> dict:
     L = load()
     o = cnd_sur_train_opts()
     L.cnd_sur_train_opts_init(C.byref(o))
@@ -647,6 +647,7 @@ def cnd_sur_train(s: CndSur, n_pairs, *, first_pair=0, set_size=(1, 50), n_trial
     o.set_size_lo, o.set_size_hi = int(set_size[0]), int(set_size[1])
     o.n_trials, o.batch_sets, o.sim_chunk, o.lr = int(n_trials), int(batch_sets), int(sim_chunk), float(lr)
     o.data_seed, o.rng_seed, o.stream = int(data_seed), int(rng_seed), stream
+    o.hub_frac = float(hub_frac)
     sim_ms, train_ms = C.c_double(), C.c_double()
     o.sim_ms_out = C.cast(C.pointer(sim_ms), C.c_void_p)
     o.train_ms_out = C.cast(C.pointer(train_ms), C.c_void_p)
@@ -658,7 +659,7 @@ def cnd_sur_train(s: CndSur, n_pairs, *, first_pair=0, set_size=(1, 50), n_trial
     return {"loss": loss[:steps], "sim_ms": sim_ms.value, "train_ms": train_ms.value}
 
 
-SCREEN_MODES = {"gradient": 0, "onehop": 1, "degree": 2}
+SCREEN_MODES = {"gradient": 0, "onehop": 1, "degree": 2, "mixed": 3}
 
 
 def cnd_ic_im_screened(g, sur, k, n_trials, rng_seed, *, n_screen=64, n_exact=4, mode="gradient", candidates=None,

@@ -277,7 +277,7 @@ cnd_status screened(const cnd_graph *g, cnd_sur *sur, const cnd_im_opts *o, cons
     const char *fn = "cnd_ic_im_screened";
     clear_error();
     if (!g || !o || !so || !seeds_out || (!sur && so->mode != 2)) {
-        set_error("%s: graph, surrogate (modes 0, 1), options and seeds_out are required", fn);
+        set_error("%s: graph, surrogate (modes 0, 1, 3), options and seeds_out are required", fn);
         return CND_EINVAL;
     }
     const cnd_graph_dev &G = g->d;
@@ -286,8 +286,8 @@ cnd_status screened(const cnd_graph *g, cnd_sur *sur, const cnd_im_opts *o, cons
         return CND_EINVAL;
     }
     if (o->n_trials < 1 || o->n_trials > INT32_MAX || so->n_exact < 1 ||
-        (so->n_screen != 0 && so->n_screen < so->n_exact) || so->mode < 0 || so->mode > 2) {
-        set_error("%s: need 1 <= n_trials <= 2^31-1, n_exact >= 1, n_screen 0 or >= n_exact, mode 0..2", fn);
+        (so->n_screen != 0 && so->n_screen < so->n_exact) || so->mode < 0 || so->mode > 3) {
+        set_error("%s: need 1 <= n_trials <= 2^31-1, n_exact >= 1, n_screen 0 or >= n_exact, mode 0..3", fn);
         return CND_EINVAL;
     }
     std::vector<int32_t> cand;
@@ -312,19 +312,21 @@ cnd_status screened(const cnd_graph *g, cnd_sur *sur, const cnd_im_opts *o, cons
     std::vector<char> is_cand((size_t)G.n, 0);
     for (int32_t v : cand) is_cand[(size_t)v] = 1;
     std::vector<int32_t> S, pool, one;
-    std::vector<float> score((size_t)G.n);
-    if (so->mode == 2) {
+    std::vector<float> score((size_t)G.n), degree;
+    if (so->mode == 2 || so->mode == 3) {
         std::vector<int32_t> rp((size_t)G.n + 1);
         CND_CUDA_TRY(cudaMemcpy(rp.data(), G.row_ptr, sizeof(int32_t) * rp.size(), cudaMemcpyDeviceToHost));
-        for (int32_t v = 0; v < G.n; ++v) score[(size_t)v] = (float)(rp[(size_t)v + 1] - rp[(size_t)v]);
+        degree.resize((size_t)G.n);
+        for (int32_t v = 0; v < G.n; ++v) degree[(size_t)v] = (float)(rp[(size_t)v + 1] - rp[(size_t)v]);
+        if (so->mode == 2) score = degree;
     }
-    std::vector<double> val;
+    std::vector<double> val, val2;
     std::vector<int64_t> F;
     double sur_ms = 0.0, sim_ms = 0.0;
     int64_t fS = 0;
     for (int32_t j = 0; j < o->k; ++j) {
         auto t0 = Clock::now();
-        if (so->mode == 0)
+        if (so->mode == 0 || so->mode == 3)
             s = cnd_sur_scores(sur, S.data(), (int32_t)S.size(), score.data());
         else if (so->mode == 1)
             s = cnd_sur_onehop(sur, S.data(), (int32_t)S.size(), score.data());
@@ -336,8 +338,22 @@ cnd_status screened(const cnd_graph *g, cnd_sur *sur, const cnd_im_opts *o, cons
                 pool.push_back(v);
                 val.push_back((double)score[(size_t)v]);
             }
-        // without a network (mode 2) the first score alone picks the candidates to simulate
-        std::vector<int32_t> keep = top_by(pool, val, so->mode == 2 ? n_exact : n_screen);
+        // without a network (mode 2) the first score alone picks the candidates to simulate; mode 3
+        // takes them alternately from the network's ranking and the out-degree ranking
+        std::vector<int32_t> keep;
+        if (so->mode == 3) {
+            val2.clear();
+            for (int32_t v : pool) val2.push_back((double)degree[(size_t)v]);
+            const std::vector<int32_t> a = top_by(pool, val, n_exact), b = top_by(pool, val2, n_exact);
+            size_t ia = 0, ib = 0;
+            while (keep.size() < std::min(n_exact, pool.size())) {
+                const bool from_a = (keep.size() % 2 == 0 && ia < a.size()) || ib >= b.size();
+                const int32_t c = from_a ? a[ia++] : b[ib++];
+                if (std::find(keep.begin(), keep.end(), c) == keep.end()) keep.push_back(c);
+            }
+        } else {
+            keep = top_by(pool, val, so->mode == 2 ? n_exact : n_screen);
+        }
         if (keep.size() > n_exact) {
             val.assign(keep.size(), 0.0);
             for (size_t i = 0; i < keep.size(); ++i) {

@@ -749,6 +749,7 @@ struct cnd_sur {
           *da0 = nullptr, *yv = nullptr;
     int32_t *seeds = nullptr;
     int32_t seeds_cap = 0;
+    std::vector<int32_t> row_ptr_h;  // host copy of the out-CSR offsets (training-set sampler)
     double *dsum = nullptr;  // [0] spread, [1] loss
     std::vector<void *> allocs;
 };
@@ -951,6 +952,7 @@ cnd_status cnd_sur_create(const cnd_graph *g, const float *params, cnd_sur **out
     std::vector<int32_t> split;
     make_items(irp, it_in, &split);
     make_items(rp, it_out, nullptr);
+    s->row_ptr_h = rp;
     s->n_items_in = (int32_t)it_in.size();
     s->n_items_out = (int32_t)it_out.size();
     s->n_split = (int32_t)split.size();
@@ -1238,16 +1240,37 @@ struct Stream {
     }
 };
 
-// seed set of pair i: size U{lo..hi}, distinct uniform nodes (Floyd's sampling)
-void pair_seeds(uint64_t data_seed, int64_t i, int32_t n, int32_t lo, int32_t hi, std::vector<int32_t> &out) {
+// seed set of pair i: size U{lo..hi}, distinct nodes.  hub_frac == 0: uniform (Floyd's sampling);
+// else each seed is, with probability hub_frac, the source of a uniform random edge (row_ptr is
+// the host copy of the out-CSR offsets: out-degree prefix sums), else a uniform node; repeats are
+// drawn again (and, should draws keep repeating, the lowest free ids fill the set).
+void pair_seeds(uint64_t data_seed, int64_t i, int32_t n, int32_t lo, int32_t hi, float hub_frac,
+                const std::vector<int32_t> &row_ptr, std::vector<int32_t> &out) {
     Stream r{splitmix64(data_seed) ^ splitmix64(0x5EEDull + (uint64_t)i)};
     const int32_t k = std::min(n, lo + (int32_t)r.below((uint32_t)(hi - lo + 1)));
     out.clear();
-    for (int32_t j = n - k; j < n; ++j) {
-        const int32_t t = (int32_t)r.below((uint32_t)j + 1);
-        bool dup = std::find(out.begin(), out.end(), t) != out.end();
-        out.push_back(dup ? j : t);
+    const int32_t m = row_ptr.empty() ? 0 : row_ptr.back();
+    if (hub_frac <= 0.0f || m == 0) {
+        for (int32_t j = n - k; j < n; ++j) {
+            const int32_t t = (int32_t)r.below((uint32_t)j + 1);
+            bool dup = std::find(out.begin(), out.end(), t) != out.end();
+            out.push_back(dup ? j : t);
+        }
+        return;
     }
+    const uint64_t cut = (uint64_t)((double)hub_frac * 16777216.0);  // hub_frac in 2^-24 units
+    for (int64_t tries = 0; (int32_t)out.size() < k && tries < 64 * (int64_t)k + 1024; ++tries) {
+        int32_t u;
+        if ((r.next() >> 40) < cut) {
+            const int32_t e = (int32_t)r.below((uint32_t)m);
+            u = (int32_t)(std::upper_bound(row_ptr.begin(), row_ptr.end(), e) - row_ptr.begin()) - 1;
+        } else {
+            u = (int32_t)r.below((uint32_t)n);
+        }
+        if (std::find(out.begin(), out.end(), u) == out.end()) out.push_back(u);
+    }
+    for (int32_t u = 0; (int32_t)out.size() < k && u < n; ++u)
+        if (std::find(out.begin(), out.end(), u) == out.end()) out.push_back(u);
 }
 
 }  // namespace
@@ -1257,7 +1280,7 @@ extern "C" cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, dou
     cnd_status st = check_sur(s, "cnd_sur_train");
     if (st != CND_OK) return st;
     if (!o || o->n_pairs < 0 || o->first_pair < 0 || o->set_size_lo < 1 || o->set_size_hi < o->set_size_lo ||
-        o->n_trials < 1) {
+        o->n_trials < 1 || !(o->hub_frac >= 0.0f && o->hub_frac <= 1.0f)) {
         set_error("cnd_sur_train: bad options");
         return CND_EINVAL;
     }
@@ -1316,7 +1339,7 @@ extern "C" cnd_status cnd_sur_train(cnd_sur *s, const cnd_sur_train_opts *o, dou
         keys.resize((size_t)cnt);
         for (int32_t i = 0; i < cnt; ++i) {
             const int64_t pid = o->first_pair + c0 + i;
-            pair_seeds(o->data_seed, pid, n, o->set_size_lo, o->set_size_hi, one);
+            pair_seeds(o->data_seed, pid, n, o->set_size_lo, o->set_size_hi, o->hub_frac, s->row_ptr_h, one);
             hs.insert(hs.end(), one.begin(), one.end());
             off.push_back((int64_t)hs.size());
             keys[(size_t)i] = o->rng_seed + (uint64_t)pid;

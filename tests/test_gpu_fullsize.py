@@ -3,8 +3,9 @@
 R-MAT scale 24 (edge factor 16: 263 M directed edges, n = 2^24; IC p = 0.01, LT weighted cascade,
 the 100 highest-out-degree seeds) and the batched R-MAT scale 20 workload (2^24 samples; IC p ~
 U[0, 0.1); the first 64 of the 4,096 seed sets) run on the GPU as bench.py times them: seeds in device
-memory, one call per model, the pass width the engine picks (three passes of 86 words for 16,384 IC
-trials at n = 2^24).  The oracle cannot run every trial at this size, so:
+memory, one call per model of 1,024 trials over a contiguous trial range, the pass width the engine
+picks; also 16,384 IC trials (three passes of 86 words at n = 2^24) and LT split into two passes.
+The oracle cannot run every trial at this size, so:
 
 - sampled trials are recomputed one by one (``first_trial = t``, one trial each) and their spreads
   must be identical -- trial ids at word, lane and pass boundaries and at the top of the 100,000;
@@ -77,18 +78,41 @@ def test_rmat24_ic_sampled_trials(rmat24):
     assert np.array_equal(spread[local], want), (local, spread[local], want)
 
 
-def test_rmat24_lt_sampled_trials(rmat24):
-    """1,024 LT trials (one pass of 16 words), trials 98,944 .. 99,967."""
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_rmat24_bench_step_sampled_trials(rmat24, model):
+    """One call of bench.py's default step: 1,024 trials, a contiguous range of trial ids (the range of
+    step 8 of the rotation, trials 8,192 .. 9,215), device seeds, the engine's own pass width; LT in the
+    counting form.  Sampled trials at word and lane boundaries and random ones."""
+    g, G, p, w, seeds = rmat24
+    T, first = 1024, 8 * 1024
+    f = P.cnd_ic_simulate_ex if model == "ic" else P.cnd_lt_simulate_ex
+    r = f(G, torch.as_tensor(seeds, device="cuda"), T, 1, first_trial=first, edge_checks=True,
+          stats=P.CND_STATS_COUNT)
+    torch.cuda.synchronize()
+    assert r.status == P.CND_OK and r.stats["passes"] == 1
+    if model == "lt":
+        assert r.stats["lt_counters"] == 1
+    spread, count = r.spread.cpu().numpy(), r.node_count.cpu().numpy()
+    _identities(g, seeds, spread, count, r.edge_checks, T)
+    rng = np.random.default_rng(26 if model == "ic" else 27)
+    local = np.unique(np.concatenate([[0, 1, 63, 64, 511, 512, 1023], rng.integers(0, T, 9)]))
+    want = _oracle_trials(model, g, seeds, 1, first + local, p=p, w=w)
+    assert np.array_equal(spread[local], want), (local, spread[local], want)
+
+
+def test_rmat24_lt_two_passes(rmat24):
+    """1,024 LT trials at the top of the 100,000 (98,944 .. 99,967) split into two passes of 8 words, so
+    the counting form re-initialises its counters and seeds between passes at full size."""
     g, G, _, w, seeds = rmat24
     T, first = 1024, 98_944
     r = P.cnd_lt_simulate_ex(G, torch.as_tensor(seeds, device="cuda"), T, 1, first_trial=first,
-                             edge_checks=True)
+                             edge_checks=True, word_bits=512, stats=P.CND_STATS_COUNT)
     torch.cuda.synchronize()
-    assert r.status == P.CND_OK
+    assert r.status == P.CND_OK and r.stats["passes"] == 2 and r.stats["lt_counters"] == 1
     spread, count = r.spread.cpu().numpy(), r.node_count.cpu().numpy()
     _identities(g, seeds, spread, count, r.edge_checks, T)
     rng = np.random.default_rng(25)
-    local = np.unique(np.concatenate([[0, 63, 64, 1023], rng.integers(0, T, 4)]))
+    local = np.unique(np.concatenate([[0, 63, 511, 512, 575, 1023], rng.integers(0, T, 2)]))
     want = _oracle_trials("lt", g, seeds, 1, first + local, w=w)
     assert np.array_equal(spread[local], want), (local, spread[local], want)
 
