@@ -341,10 +341,11 @@ cnd_status cnd_lt_im_celf(const cnd_graph *g, const cnd_im_opts *o, int32_t *see
  * its working memory (about 0.5 KB per node).  The graph needs IC
  * probabilities.  Seed ids must lie in [0, n); duplicates count once.
  *
- * Not bit-reproducible: in-edge sums of high in-degree nodes are split over
- * several warps and gradients are summed over blocks, both with fp32 atomic
- * adds, so results can differ in their last bits between runs (and a bf16
- * rounding of a sum by one unit).  Simulation results above are exact.
+ * Bit-reproducible: every sum runs in a fixed order (in-edge sums of high
+ * in-degree nodes split over several warps, gradients split over blocks and
+ * the predicted spread are added up from partial sums in index order; the
+ * seed channel of a^1 is an exact fixed-point sum), so the same calls on the
+ * same device give the same bits.  Simulation results above are exact.
  */
 #define CND_SUR_N_PARAMS 18689
 typedef struct cnd_sur cnd_sur;

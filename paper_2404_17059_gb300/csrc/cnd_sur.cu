@@ -5,7 +5,8 @@
 // layer-1 inputs x, a^1: n x 16 bf16).  Each layer is two kernels:
 //   k_spmm_in    a = A_q h over the in-CSR (warp per work item of <= 256
 //                in-edges; a node with more in-edges is split over several
-//                items that add into an fp32 scratch row, rounded afterwards);
+//                items, each writing its partial row, summed in item order
+//                and rounded afterwards);
 //   k_dense_fwd  the 64 x (2 DIN) dense map on the tensor cores
 //                (mma.sync m16n8k16 bf16 -> fp32, a warp per 16-row tile) with
 //                bias, relu and bf16 rounding fused; the last layer also
@@ -16,6 +17,9 @@
 // transpose aggregation over the out-CSR).  The seed-dependent channel of
 // layer 1 (x_v[0] = s_v and a^1_v[0]) is patched in place from the seeds'
 // out-edges; the static channels are built once.
+// Every reduction runs in a fixed order (partial rows and per-block partial
+// sums are added up in index order by a second kernel; the seed channel sums
+// fixed-point integers), so results do not depend on scheduling.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -139,10 +143,11 @@ __global__ void k_pack_weights(const float *__restrict__ p, __nv_bfloat16 *__res
 }
 
 // --------------------------------------------------------------------------- seed channel
-// phase 1: x_u[0] = 1 for seeds; acc0[w] += q over the seeds' out-edges
+// phase 1: x_u[0] = 1 for seeds; acc0[w] += q * 2^32 over the seeds' out-edges.  q = fp32(thr) 2^-32
+// with fp32(thr) an integer below 2^33, so the sums are exact integers: their order does not matter.
 __global__ void k_seed_scatter(const int32_t *__restrict__ seeds, int32_t ns, const int32_t *__restrict__ row_ptr,
                                const uint2 *__restrict__ ic_edge, __nv_bfloat16 *__restrict__ x,
-                               float *__restrict__ acc0) {
+                               unsigned long long *__restrict__ acc0) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -151,16 +156,17 @@ __global__ void k_seed_scatter(const int32_t *__restrict__ seeds, int32_t ns, co
         if (lane == 0) x[(size_t)u * D0] = __float2bfloat16_rn(1.0f);
         for (int32_t e = row_ptr[u] + lane; e < row_ptr[u + 1]; e += 32) {
             const uint2 ed = ic_edge[e];
-            atomicAdd(acc0 + ed.x, edge_q(ed.y));
+            atomicAdd(acc0 + ed.x, (unsigned long long)__uint2float_rn(ed.y));
         }
     }
 }
 
-// phase 2: a^1_w[0] = bf16(acc0[w]) for the seeds' out-neighbours; mode 1 clears everything phase 1 set
+// phase 2: a^1_w[0] = bf16(acc0[w] 2^-32) (exact in fp64, one rounding) for the seeds' out-neighbours;
+// mode 1 clears everything phase 1 set
 template <int CLEAR>
 __global__ void k_seed_finish(const int32_t *__restrict__ seeds, int32_t ns, const int32_t *__restrict__ row_ptr,
                               const uint2 *__restrict__ ic_edge, __nv_bfloat16 *__restrict__ x,
-                              __nv_bfloat16 *__restrict__ a1, float *__restrict__ acc0) {
+                              __nv_bfloat16 *__restrict__ a1, unsigned long long *__restrict__ acc0) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -171,9 +177,9 @@ __global__ void k_seed_finish(const int32_t *__restrict__ seeds, int32_t ns, con
             const uint32_t w = ic_edge[e].x;
             if (CLEAR) {
                 a1[(size_t)w * D0] = __float2bfloat16_rn(0.0f);
-                acc0[w] = 0.0f;
+                acc0[w] = 0ull;
             } else {
-                a1[(size_t)w * D0] = __float2bfloat16_rn(acc0[w]);
+                a1[(size_t)w * D0] = __double2bfloat16((double)acc0[w] * 2.3283064365386963e-10);
             }
         }
     }
@@ -181,7 +187,7 @@ __global__ void k_seed_finish(const int32_t *__restrict__ seeds, int32_t ns, con
 
 // --------------------------------------------------------------------------- aggregation
 struct Item {
-    int32_t node, begin, end, slot;  // slot >= 0: partial row of a split node (scratch row index)
+    int32_t node, begin, end, slot;  // slot >= 0: this item's partial row of a split node (scratch row index)
 };
 
 // a[v] = bf16(sum over in-edges of q h[src]) for 64-wide bf16 rows; a warp per item.  The warp
@@ -243,33 +249,62 @@ __global__ void __launch_bounds__(256) k_spmm_in(int32_t n_items, const Item *__
                 o.w = pack_bf16(acc[6], acc[7]);
                 *reinterpret_cast<uint4 *>(a + (size_t)item.node * H + f8) = o;
             } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) atomicAdd(scratch + (size_t)item.slot * H + f8 + i, acc[i]);
+                float4 *pr = reinterpret_cast<float4 *>(scratch + (size_t)item.slot * H + f8);
+                pr[0] = make_float4(acc[0], acc[1], acc[2], acc[3]);
+                pr[1] = make_float4(acc[4], acc[5], acc[6], acc[7]);
             }
         }
     }
 }
 
-// rows of split nodes: round the fp32 sums into a, and clear the scratch for the next call
-__global__ void k_split_finish(int32_t n_split, const int32_t *__restrict__ split_node, float *__restrict__ scratch,
+// rows of split nodes: add the partial rows of node i (slots first[i] .. first[i+1]-1) in order,
+// round into a
+__global__ void k_split_finish(int32_t n_split, const int32_t *__restrict__ split_node,
+                               const int32_t *__restrict__ first, const float *__restrict__ scratch,
                                __nv_bfloat16 *__restrict__ a) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int i = warp; i < n_split; i += nwarps) {
-        float2 *row = reinterpret_cast<float2 *>(scratch + (size_t)i * H);
-        const float2 f = row[lane];
-        row[lane] = make_float2(0.0f, 0.0f);
+        float2 f = make_float2(0.0f, 0.0f);
+        for (int32_t j = first[i]; j < first[i + 1]; ++j) {
+            const float2 x = reinterpret_cast<const float2 *>(scratch + (size_t)j * H)[lane];
+            f.x += x.x;
+            f.y += x.y;
+        }
         *reinterpret_cast<uint32_t *>(a + (size_t)split_node[i] * H + 2 * lane) = pack_bf16(f.x, f.y);
     }
 }
 
+// out-rows of split nodes: dh[node i] += the partial rows of node i, in order
+__global__ void k_split_out_finish(int32_t n_split, const int32_t *__restrict__ split_node,
+                                   const int32_t *__restrict__ first, const float *__restrict__ scratch,
+                                   float *__restrict__ dh) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = warp; i < n_split; i += nwarps) {
+        float2 f = make_float2(0.0f, 0.0f);
+        for (int32_t j = first[i]; j < first[i + 1]; ++j) {
+            const float2 x = reinterpret_cast<const float2 *>(scratch + (size_t)j * H)[lane];
+            f.x += x.x;
+            f.y += x.y;
+        }
+        float2 *row = reinterpret_cast<float2 *>(dh + (size_t)split_node[i] * H) + lane;
+        float2 v = *row;
+        v.x += f.x;
+        v.y += f.y;
+        *row = v;
+    }
+}
+
 // dh[u] += sum over out-edges (u -> w) of q da[w], 64-wide fp32 rows; a warp per item of the out-CSR,
-// 2 rows per load instruction (16 lanes x 16 B per 256-byte row), 8 rows in flight.  Items of a
-// split node add with atomics; a single-item node is read-modify-written by its warp.
+// 2 rows per load instruction (16 lanes x 16 B per 256-byte row), 8 rows in flight.  An item of a
+// split node writes its partial row (k_split_out_finish adds them in order); a single-item node is
+// read-modify-written by its warp.
 __global__ void __launch_bounds__(256) k_spmm_out(int32_t n_items, const Item *__restrict__ items,
                                                   const uint2 *__restrict__ ic_edge, const float *__restrict__ da,
-                                                  float *__restrict__ dh) {
+                                                  float *__restrict__ dh, float *__restrict__ scratch) {
     const int lane = threadIdx.x & 31;
     const int sub = lane >> 4;       // which of 2 edges
     const int f4 = (lane & 15) * 4;  // first of this lane's 4 features
@@ -317,11 +352,7 @@ __global__ void __launch_bounds__(256) k_spmm_out(int32_t n_items, const Item *_
                 v.w += acc.w;
                 *row = v;
             } else {
-                float *r = dh + (size_t)item.node * H + f4;
-                atomicAdd(r, acc.x);
-                atomicAdd(r + 1, acc.y);
-                atomicAdd(r + 2, acc.z);
-                atomicAdd(r + 3, acc.w);
+                *reinterpret_cast<float4 *>(scratch + (size_t)item.slot * H + f4) = acc;
             }
         }
     }
@@ -450,13 +481,16 @@ __device__ __forceinline__ float head_grad(const HeadArgs &ha, int r, bool ok, f
 // from the head).  GRADS: e = bf16(dz) stored for k_dw, bias (and head) gradients accumulated.
 // XOUT 1: dX = e [W_s | W_n] -> dh_prev (first DIN columns) and da (last DIN); XOUT 2: column 0 of
 // each half only -> ds0, da0 (the seed channel, for screening).
+// GRADS: block b writes its partial sums to part[b * kBwdPart ..] (bias 64, w_o 64, b_o 1, loss 1);
+// k_reduce_bwd adds them up in block order.
+constexpr int kBwdPart = 2 * H + 2;
 template <int DIN, int MODE, int XOUT, bool GRADS>
 __global__ void __launch_bounds__(128) k_dense_bwd(int32_t n, const __nv_bfloat16 *__restrict__ hout,
                                                    const float *__restrict__ dh, HeadArgs ha,
                                                    const __nv_bfloat16 *__restrict__ wt, int layer,
                                                    const float *__restrict__ params, __nv_bfloat16 *__restrict__ e_out,
                                                    float *__restrict__ dprev, float *__restrict__ da,
-                                                   float *__restrict__ grad) {
+                                                   float *__restrict__ part) {
     using T = WTile<DIN>;
     __shared__ __align__(16) __nv_bfloat16 swt[(XOUT ? T::K : 1) * T::LDT];
     __shared__ float swo[H];
@@ -549,7 +583,7 @@ __global__ void __launch_bounds__(128) k_dense_bwd(int32_t n, const __nv_bfloat1
     }
     if (GRADS) {
         // reduce over the 8 row groups (lanes with equal t), then over the block's warps in shared
-        // memory, then one atomic per column per block
+        // memory, in a fixed order; the block's sums go to its partial row
         __shared__ float s_db[4][H], s_dwo[4][H], s_misc[4][2];
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
@@ -581,34 +615,37 @@ __global__ void __launch_bounds__(128) k_dense_bwd(int32_t n, const __nv_bfloat1
         }
         __syncthreads();
         const int nw = blockDim.x >> 5;
+        float *pb = part + (size_t)blockIdx.x * kBwdPart;
         if (threadIdx.x < H) {
             float a = 0.0f, b = 0.0f;
             for (int w = 0; w < nw; ++w) {
                 a += s_db[w][threadIdx.x];
                 b += s_dwo[w][threadIdx.x];
             }
-            atomicAdd(grad + off_b(layer) + threadIdx.x, a);
-            if (MODE == 1) atomicAdd(grad + OFF_WO + threadIdx.x, b);
+            pb[threadIdx.x] = a;
+            pb[H + threadIdx.x] = MODE == 1 ? b : 0.0f;
         }
-        if (MODE == 1 && threadIdx.x == 0) {
+        if (threadIdx.x == 0) {
             float a = 0.0f, b = 0.0f;
-            for (int w = 0; w < nw; ++w) {
-                a += s_misc[w][0];
-                b += s_misc[w][1];
-            }
-            atomicAdd(grad + OFF_BO, a);
-            atomicAdd(ha.loss, (double)b * (double)ha.loss_scale);
+            if (MODE == 1)
+                for (int w = 0; w < nw; ++w) {
+                    a += s_misc[w][0];
+                    b += s_misc[w][1];
+                }
+            pb[2 * H] = a;
+            pb[2 * H + 1] = b;
         }
     }
 }
 
-// dW[o][i] += sum_r e[r][o] X[r][i], X = [h_prev | a] (split-K over row chunks; 8 warps per block,
-// warp w owns outputs o in [16 (w % 4), +16) and inputs i in [K/2 (w / 4), +K/2))
+// dW[o][i] = sum_r e[r][o] X[r][i], X = [h_prev | a] (split-K over row chunks; 8 warps per block,
+// warp w owns outputs o in [16 (w % 4), +16) and inputs i in [K/2 (w / 4), +K/2)); block b writes its
+// partial dW (64 x 2 DIN, row-major) to part[b * 128 DIN ..], added up in block order by k_reduce_dw
 template <int DIN>
 __global__ void __launch_bounds__(256) k_dw(int32_t n, const __nv_bfloat16 *__restrict__ e,
                                             const __nv_bfloat16 *__restrict__ hprev,
-                                            const __nv_bfloat16 *__restrict__ ain, int layer,
-                                            float *__restrict__ grad, int rows_per_block) {
+                                            const __nv_bfloat16 *__restrict__ ain, float *__restrict__ part,
+                                            int rows_per_block) {
     constexpr int K = 2 * DIN;
     constexpr int LE = H + 8, LX = K + 8;
     constexpr int NT = K / 2 / 8;  // n-tiles per warp
@@ -660,21 +697,52 @@ __global__ void __launch_bounds__(256) k_dw(int32_t n, const __nv_bfloat16 *__re
         }
         __syncthreads();
     }
+    float *pb = part + (size_t)blockIdx.x * (H * K);
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int o = o0 + g + (q >= 2 ? 8 : 0);
             const int i = i0 + j * 8 + 2 * t + (q & 1);
-            const int idx = i < DIN ? off_ws(layer) + o * DIN + i : off_wn(layer) + o * DIN + (i - DIN);
-            atomicAdd(grad + idx, acc[j][q]);
+            pb[o * K + i] = acc[j][q];
         }
     }
 }
 
+// grad += the blocks' partial dW of layer `layer`, added in block order (a thread per weight)
+__global__ void k_reduce_dw(int32_t nblocks, int32_t din, const float *__restrict__ part, int layer,
+                            float *__restrict__ grad) {
+    const int K = 2 * din;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < H * K; idx += gridDim.x * blockDim.x) {
+        float sum = 0.0f;
+        for (int b = 0; b < nblocks; ++b) sum += part[(size_t)b * H * K + idx];
+        const int o = idx / K, i = idx % K;
+        grad[i < din ? off_ws(layer) + o * din + i : off_wn(layer) + o * din + (i - din)] += sum;
+    }
+}
+
+// grad (bias of `layer`; MODE 1 also w_o, b_o and the loss) += the blocks' partial sums, in block order
+__global__ void k_reduce_bwd(int32_t nblocks, const float *__restrict__ part, int layer, int head,
+                             float *__restrict__ grad, double *__restrict__ loss, float loss_scale) {
+    const int c = threadIdx.x;  // 0 .. 2 H + 1
+    if (c >= kBwdPart || (!head && c >= H)) return;
+    if (c < 2 * H + 1) {
+        float sum = 0.0f;
+        for (int b = 0; b < nblocks; ++b) sum += part[(size_t)b * kBwdPart + c];
+        grad[c < H ? off_b(layer) + c : (c < 2 * H ? OFF_WO + (c - H) : OFF_BO)] += sum;
+    } else {
+        double sum = 0.0;
+        for (int b = 0; b < nblocks; ++b) sum += (double)part[(size_t)b * kBwdPart + c];
+        *loss += sum * (double)loss_scale;
+    }
+}
+
 // yhat and the predicted spread; screening scores
-__global__ void k_yhat(int32_t n, const float *__restrict__ o, const __nv_bfloat16 *__restrict__ x,
-                       float *__restrict__ yhat, double *__restrict__ spread) {
+// yhat, and each block's sum of it in part[block] (256 threads; k_sum_parts adds the blocks in order)
+__global__ void __launch_bounds__(256) k_yhat(int32_t n, const float *__restrict__ o,
+                                              const __nv_bfloat16 *__restrict__ x, float *__restrict__ yhat,
+                                              double *__restrict__ part) {
+    __shared__ double s_w[8];
     double local = 0.0;
     for (int32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
         const float s = __bfloat162float(x[(size_t)v * D0]);
@@ -683,7 +751,19 @@ __global__ void k_yhat(int32_t n, const float *__restrict__ o, const __nv_bfloat
         local += y;
     }
     for (int off = 16; off; off >>= 1) local += __shfl_down_sync(0xffffffffu, local, off);
-    if ((threadIdx.x & 31) == 0) atomicAdd(spread, local);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = local;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double b = 0.0;
+        for (int w = 0; w < 8; ++w) b += s_w[w];
+        part[blockIdx.x] = b;
+    }
+}
+
+__global__ void k_sum_parts(int32_t nblocks, const double *__restrict__ part, double *__restrict__ out) {
+    double sum = 0.0;
+    for (int b = 0; b < nblocks; ++b) sum += part[b];
+    *out = sum;
 }
 
 __global__ void k_scores(int32_t n, const float *__restrict__ o, const __nv_bfloat16 *__restrict__ x,
@@ -739,13 +819,20 @@ struct cnd_sur {
     uint2 *in_c = nullptr;
     Item *items_in = nullptr, *items_out = nullptr;
     int32_t n_items_in = 0, n_items_out = 0;
-    int32_t *split_node = nullptr;
+    int32_t *split_node = nullptr, *split_first = nullptr;  // in-CSR split nodes, first partial row of each
     int32_t n_split = 0;
-    float *scratch = nullptr;
+    float *scratch = nullptr;                                 // partial rows of the in-aggregation
+    int32_t *split_out_node = nullptr, *split_out_first = nullptr;
+    int32_t n_split_out = 0;
+    float *scratch_out = nullptr;                             // partial rows of the out-aggregation
+    float *part = nullptr;                                    // per-block partial sums of the backward
+    double *part_d = nullptr;                                 // per-block partial sums of the spread
+    int32_t part_blocks = 0;                                  // blocks the backward's partials allow
     // activations
     __nv_bfloat16 *x = nullptr, *a1 = nullptr, *h[3] = {nullptr, nullptr, nullptr}, *a[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16 *e = nullptr;
-    float *o = nullptr, *acc0 = nullptr, *dhA = nullptr, *dhB = nullptr, *da = nullptr, *ds0 = nullptr,
+    unsigned long long *acc0 = nullptr;
+    float *o = nullptr, *dhA = nullptr, *dhB = nullptr, *da = nullptr, *ds0 = nullptr,
           *da0 = nullptr, *yv = nullptr;
     int32_t *seeds = nullptr;
     int32_t seeds_cap = 0;
@@ -772,18 +859,24 @@ void free_all(cnd_sur *s) {
     s->allocs.clear();
 }
 
-// work items of <= kItemEdges edges per node (rows with more edges are split; split rows get slots)
-void make_items(const std::vector<int32_t> &rp, std::vector<Item> &items, std::vector<int32_t> *split) {
+// work items of <= kItemEdges edges per node; a row with more edges is split, each of its items
+// getting a partial-row slot of its own (consecutive per node): split[i] is the i-th split node and
+// first[i] .. first[i+1]-1 its slots
+void make_items(const std::vector<int32_t> &rp, std::vector<Item> &items, std::vector<int32_t> &split,
+                std::vector<int32_t> &first) {
     const int32_t n = (int32_t)rp.size() - 1;
     items.clear();
+    split.clear();
+    first.assign(1, 0);
+    int32_t slot = 0;
     for (int32_t v = 0; v < n; ++v) {
         const int32_t b = rp[v], e = rp[v + 1];
         if (e - b <= kItemEdges) {
             items.push_back({v, b, e, -1});
         } else {
-            const int32_t slot = split ? (int32_t)split->size() : 0;
-            if (split) split->push_back(v);
-            for (int32_t k = b; k < e; k += kItemEdges) items.push_back({v, k, std::min(e, k + kItemEdges), slot});
+            split.push_back(v);
+            for (int32_t k = b; k < e; k += kItemEdges) items.push_back({v, k, std::min(e, k + kItemEdges), slot++});
+            first.push_back(slot);
         }
     }
 }
@@ -853,8 +946,8 @@ void aggregate_in(cnd_sur *s, const __nv_bfloat16 *hin, __nv_bfloat16 *aout, cud
     const int blocks = grid_for((int64_t)s->n_items_in * 32, 256, s->num_sms);
     k_spmm_in<<<blocks, 256, 0, st>>>(s->n_items_in, s->items_in, s->in_c, hin, aout, s->scratch);
     if (s->n_split)
-        k_split_finish<<<grid_for((int64_t)s->n_split * 32, 256, s->num_sms), 256, 0, st>>>(s->n_split, s->split_node,
-                                                                                            s->scratch, aout);
+        k_split_finish<<<grid_for((int64_t)s->n_split * 32, 256, s->num_sms), 256, 0, st>>>(
+            s->n_split, s->split_node, s->split_first, s->scratch, aout);
 }
 
 void forward(cnd_sur *s, cudaStream_t st) {
@@ -870,7 +963,17 @@ void forward(cnd_sur *s, cudaStream_t st) {
 
 void aggregate_out(cnd_sur *s, const float *da, float *dh, cudaStream_t st) {
     const int blocks = grid_for((int64_t)s->n_items_out * 32, 256, s->num_sms);
-    k_spmm_out<<<blocks, 256, 0, st>>>(s->n_items_out, s->items_out, s->g->d.ic_edge, da, dh);
+    k_spmm_out<<<blocks, 256, 0, st>>>(s->n_items_out, s->items_out, s->g->d.ic_edge, da, dh, s->scratch_out);
+    if (s->n_split_out)
+        k_split_out_finish<<<grid_for((int64_t)s->n_split_out * 32, 256, s->num_sms), 256, 0, st>>>(
+            s->n_split_out, s->split_out_node, s->split_out_first, s->scratch_out, dh);
+}
+
+// the predicted spread (sum of yhat) into *spread, summed in a fixed order
+void spread_sum(cnd_sur *s, double *spread, cudaStream_t st) {
+    const int nb = grid_for(s->n, 256, s->num_sms);
+    k_yhat<<<nb, 256, 0, st>>>(s->n, s->o, s->x, s->yv, s->part_d);
+    k_sum_parts<<<1, 1, 0, st>>>(nb, s->part_d, spread);
 }
 
 // training backward: gradients accumulate into s->grad; loss adds into s->dsum[1]
@@ -883,15 +986,28 @@ void backward_loss(cnd_sur *s, const float *y, const int32_t *cnt, float inv_t, 
     HeadArgs ha{s->o, s->x, y, cnt, inv_t, 2.0f / (float)n / batch, s->dsum + 1, 1.0f / (float)n / batch};
     HeadArgs none{};
     __nv_bfloat16 *wt2 = s->wt + 64 * 32 + 64 * 128, *wt1 = s->wt + 64 * 32;
-    k_dense_bwd<H, 1, 1, true><<<tbb, 128, 0, st>>>(n, s->h[2], nullptr, ha, wt2, 2, s->p, s->e, s->dhA, s->da, s->grad);
-    k_dw<H><<<db, 256, 0, st>>>(n, s->e, s->h[1], s->a[2], 2, s->grad, rpb);
+    // each gradient kernel writes per-block partial sums; the reduce kernels add them up in block order
+    auto bias = [&](int layer, int head) {
+        k_reduce_bwd<<<1, 2 * H + 2, 0, st>>>(tbb, s->part, layer, head, s->grad, ha.loss, ha.loss_scale);
+    };
+    auto weights = [&](int layer, int din) {
+        k_reduce_dw<<<grid_for(H * 2 * din, 256, s->num_sms), 256, 0, st>>>(db, din, s->part, layer, s->grad);
+    };
+    k_dense_bwd<H, 1, 1, true><<<tbb, 128, 0, st>>>(n, s->h[2], nullptr, ha, wt2, 2, s->p, s->e, s->dhA, s->da, s->part);
+    bias(2, 1);
+    k_dw<H><<<db, 256, 0, st>>>(n, s->e, s->h[1], s->a[2], s->part, rpb);
+    weights(2, H);
     aggregate_out(s, s->da, s->dhA, st);
-    k_dense_bwd<H, 0, 1, true><<<tbb, 128, 0, st>>>(n, s->h[1], s->dhA, none, wt1, 1, s->p, s->e, s->dhB, s->da, s->grad);
-    k_dw<H><<<db, 256, 0, st>>>(n, s->e, s->h[0], s->a[1], 1, s->grad, rpb);
+    k_dense_bwd<H, 0, 1, true><<<tbb, 128, 0, st>>>(n, s->h[1], s->dhA, none, wt1, 1, s->p, s->e, s->dhB, s->da, s->part);
+    bias(1, 0);
+    k_dw<H><<<db, 256, 0, st>>>(n, s->e, s->h[0], s->a[1], s->part, rpb);
+    weights(1, H);
     aggregate_out(s, s->da, s->dhB, st);
     k_dense_bwd<D0, 0, 0, true><<<tbb, 128, 0, st>>>(n, s->h[0], s->dhB, none, s->wt, 0, s->p, s->e, nullptr, nullptr,
-                                                     s->grad);
-    k_dw<D0><<<db, 256, 0, st>>>(n, s->e, s->x, s->a1, 0, s->grad, rpb);
+                                                     s->part);
+    bias(0, 0);
+    k_dw<D0><<<db, 256, 0, st>>>(n, s->e, s->x, s->a1, s->part, rpb);
+    weights(0, D0);
 }
 
 void pack_weights(cnd_sur *s, cudaStream_t st) {
@@ -949,13 +1065,20 @@ cnd_status cnd_sur_create(const cnd_graph *g, const float *params, cnd_sur **out
         cudaSuccess)
         return fail(e, "in_row_ptr");
     std::vector<Item> it_in, it_out;
-    std::vector<int32_t> split;
-    make_items(irp, it_in, &split);
-    make_items(rp, it_out, nullptr);
+    std::vector<int32_t> split, first, split_out, first_out;
+    make_items(irp, it_in, split, first);
+    make_items(rp, it_out, split_out, first_out);
     s->row_ptr_h = rp;
     s->n_items_in = (int32_t)it_in.size();
     s->n_items_out = (int32_t)it_out.size();
     s->n_split = (int32_t)split.size();
+    s->n_split_out = (int32_t)split_out.size();
+    // per-block partials: the backward's blocks (bias rows, dW blocks), the spread's blocks
+    const int bwd_blocks = grid_for(((int64_t)n + 15) / 16 * 32, 128, s->num_sms, 4);
+    const int rpb0 = (int)std::max<int64_t>(512, (((int64_t)n + 2 * s->num_sms - 1) / (2 * s->num_sms) + 31) / 32 * 32);
+    const int dw_blocks = (int)std::max<int64_t>(1, ((int64_t)n + rpb0 - 1) / rpb0);
+    const size_t part_floats = std::max<size_t>((size_t)bwd_blocks * kBwdPart, (size_t)dw_blocks * H * 2 * H);
+    s->part_blocks = bwd_blocks;
     s->seeds_cap = n;
     const size_t nr = (size_t)n;
 #define SUR_ALLOC(ptr, count)                                               \
@@ -970,7 +1093,13 @@ cnd_status cnd_sur_create(const cnd_graph *g, const float *params, cnd_sur **out
     SUR_ALLOC(s->items_in, it_in.size());
     SUR_ALLOC(s->items_out, it_out.size());
     SUR_ALLOC(s->split_node, split.size());
-    SUR_ALLOC(s->scratch, split.size() * H);
+    SUR_ALLOC(s->split_first, first.size());
+    SUR_ALLOC(s->scratch, (size_t)first.back() * H);
+    SUR_ALLOC(s->split_out_node, split_out.size());
+    SUR_ALLOC(s->split_out_first, first_out.size());
+    SUR_ALLOC(s->scratch_out, (size_t)first_out.back() * H);
+    SUR_ALLOC(s->part, part_floats);
+    SUR_ALLOC(s->part_d, (size_t)grid_for(n, 256, s->num_sms));
     SUR_ALLOC(s->x, nr * D0);
     SUR_ALLOC(s->a1, nr * D0);
     for (int l = 0; l < 3; ++l) SUR_ALLOC(s->h[l], nr * H);
@@ -993,13 +1122,13 @@ cnd_status cnd_sur_create(const cnd_graph *g, const float *params, cnd_sur **out
     if ((e = cudaMemcpy(s->items_out, it_out.data(), sizeof(Item) * it_out.size(), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return fail(e, "items");
-    if (!split.empty() &&
-        (e = cudaMemcpy(s->split_node, split.data(), sizeof(int32_t) * split.size(), cudaMemcpyHostToDevice)) !=
-            cudaSuccess)
+    auto up = [&](int32_t *dst, const std::vector<int32_t> &src) {
+        return src.empty() ? cudaSuccess : cudaMemcpy(dst, src.data(), sizeof(int32_t) * src.size(), cudaMemcpyHostToDevice);
+    };
+    if ((e = up(s->split_node, split)) != cudaSuccess || (e = up(s->split_first, first)) != cudaSuccess ||
+        (e = up(s->split_out_node, split_out)) != cudaSuccess || (e = up(s->split_out_first, first_out)) != cudaSuccess)
         return fail(e, "split rows");
-    if ((e = cudaMemset(s->scratch, 0, sizeof(float) * std::max<size_t>(1, split.size() * H))) != cudaSuccess)
-        return fail(e, "memset");
-    if ((e = cudaMemset(s->acc0, 0, sizeof(float) * nr)) != cudaSuccess) return fail(e, "memset");
+    if ((e = cudaMemset(s->acc0, 0, sizeof(unsigned long long) * nr)) != cudaSuccess) return fail(e, "memset");
     const int sms = s->num_sms;
     if (m > 0) k_in_compact<<<grid_for(m, 256, sms), 256>>>(m, G.in_edge, s->in_c);
     k_features<<<grid_for(n, 256, sms), 256>>>(n, G.row_ptr, G.in_row_ptr, s->x);
@@ -1074,8 +1203,7 @@ cnd_status cnd_sur_forward(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, fl
     if ((st = upload_seeds(s, seeds, n_seeds, ns, cs, "cnd_sur_forward")) != CND_OK) return st;
     seed_set(s, s->seeds, ns, cs);
     forward(s, cs);
-    CND_CUDA_TRY(cudaMemsetAsync(s->dsum, 0, sizeof(double), cs));
-    k_yhat<<<grid_for(s->n, 256, s->num_sms), 256, 0, cs>>>(s->n, s->o, s->x, s->yv, s->dsum);
+    spread_sum(s, s->dsum, cs);
     seed_clear(s, s->seeds, ns, cs);
     CND_CUDA_TRY(cudaGetLastError());
     if (yhat_out) CND_CUDA_TRY(cudaMemcpyAsync(yhat_out, s->yv, sizeof(float) * s->n, cudaMemcpyDeviceToHost, cs));
@@ -1191,8 +1319,7 @@ cnd_status cnd_sur_onehop(cnd_sur *s, const int32_t *seeds, int32_t n_seeds, flo
     const int32_t n = s->n;
     seed_set(s, s->seeds, ns, cs);
     forward(s, cs);
-    CND_CUDA_TRY(cudaMemsetAsync(s->dsum, 0, sizeof(double), cs));
-    k_yhat<<<grid_for(n, 256, s->num_sms), 256, 0, cs>>>(n, s->o, s->x, s->yv, s->dsum);
+    spread_sum(s, s->dsum, cs);
     const cnd_graph_dev &G = s->g->d;
     k_onehop<<<grid_for(n, 256, s->num_sms), 256, 0, cs>>>(n, G.row_ptr, G.ic_edge, s->yv, s->ds0);
     seed_clear(s, s->seeds, ns, cs);

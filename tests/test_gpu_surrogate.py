@@ -135,6 +135,30 @@ def test_training_reduces_loss():
     assert loss[-16:].mean() < 0.5 * loss[:4].mean()
 
 
+def test_bit_reproducible():
+    """Every reduction runs in a fixed order: two trainings from the same start on the same data end in the
+    same bits, and forward passes, gradients and screening scores repeat bit for bit (R-MAT hubs: in-rows
+    and out-rows split over several work items, many seeds sharing out-neighbours)."""
+    g, p = _graph("rmat")
+    G = P.cnd_graph_create(g.n, g.row_ptr, g.col, p, None)
+    init = I.surrogate_init(3)
+    runs = []
+    for _ in range(2):
+        sur = P.cnd_sur_create(G, init)
+        r = P.cnd_sur_train(sur, 512, set_size=(1, 30), n_trials=128, batch_sets=16, lr=3e-3, hub_frac=0.5)
+        runs.append((P.cnd_sur_get_params(sur), r["loss"], sur))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    sur = runs[0][2]
+    seeds = I.top_degree_seeds(g, 40)
+    y = np.random.default_rng(3).uniform(0, 1, size=g.n).astype(np.float32)
+    a = [P.cnd_sur_forward(sur, seeds) for _ in range(2)]
+    assert np.array_equal(a[0][0], a[1][0]) and a[0][1] == a[1][1]
+    b = [P.cnd_sur_loss_grad(sur, seeds, y) for _ in range(2)]
+    assert b[0][0] == b[1][0] and np.array_equal(b[0][1], b[1][1])
+    c = [P.cnd_sur_scores(sur, seeds) for _ in range(2)]
+    assert np.array_equal(c[0], c[1])
+
+
 def test_onehop_scores_match_oracle(setup):
     g, OG, G, sur, params = setup
     seeds = _seeds(g, 9, 41)
