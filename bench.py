@@ -94,14 +94,16 @@ class Workload:
     [r T, (r + 1) T) with r = (i * world + rank) mod floor(total / T), so that successive steps (and
     ranks) rotate through the configuration's trials via first_trial."""
 
-    def __init__(self, name, desc, g, models, seeds=None, trials=None, rng_seed=1, batch=None, cpu=None, total=0):
+    def __init__(self, name, desc, g, models, seeds=None, trials=None, rng_seed=1, batch=None, cpu=None, total=0,
+                 ref=None):
         self.name, self.desc, self.g = name, desc, g
         self.models = models          # {"ic": p or None, "lt": w or None}
         self.seeds, self.rng_seed = seeds, rng_seed
         self.trials = dict(trials or {})
         self.total = total
         self.batch = batch            # (seed_off, seeds, trials, keys) or None
-        self.cpu = cpu or {}          # CPU-oracle sample sizes
+        self.cpu = cpu or {}          # CPU-oracle sample sizes (the cpu_baseline of our arm)
+        self.ref = ref or self.cpu    # the reference arm's sample per step
 
     def create(self, P):
         return P.cnd_graph_create(self.g.n, self.g.row_ptr, self.g.col, self.models.get("ic"),
@@ -173,7 +175,7 @@ def make_workload(name: str, trials: int = 0, items: int = 0, lt_trials: int = 0
                   f"p=1/indeg) and LT (uint32 floor((2^32-1)/indeg)), 50 top-degree seeds, {T['ic']} IC and "
                   f"{T['lt']} LT trials per step, rng_seed=1",
             g, {"ic": I.ic_weighted_cascade(g), "lt": I.lt_weighted_cascade(g)}, seeds=I.top_degree_seeds(g, 50),
-            trials=T, cpu={"ic": 2048, "lt": 1536}, total=10_000)
+            trials=T, cpu={"ic": 2048, "lt": 1536}, total=10_000, ref={"ic": 384, "lt": 256})
     if name == "er1k":
         g = I.erdos_renyi_m(1000, 10_000, graph_seed=1)
         T = {"ic": trials or 1000, "lt": lt_trials or trials or 1000}
@@ -191,7 +193,7 @@ def make_workload(name: str, trials: int = 0, items: int = 0, lt_trials: int = 0
                   f"each step simulates a contiguous range of {T['ic']} IC and {T['lt']} LT trial ids, the ranges "
                   f"rotating through the 100000 via first_trial",
             g, {"ic": I.ic_uniform(g, 0.01), "lt": I.lt_weighted_cascade(g)}, seeds=I.top_degree_seeds(g, 100),
-            trials=T, cpu={"ic": 16, "lt": 16}, total=100_000)
+            trials=T, cpu={"ic": 16, "lt": 16}, total=100_000, ref={"ic": 8, "lt": 8})
     if name == "rmat20batch":
         g = I.rmat(20, 1 << 24, graph_seed=1)
         so, seeds, tr, keys = I.batch_items(g.n, 4096, 1, 100, (256, 1024, 4096), graph_seed=1)
@@ -361,6 +363,7 @@ def run_reference(args):
         return 0
     wl = select_models(make_workload(args.workload, args.trials, args.items, args.lt_trials, args.scale),
                        args.models)
+    wl.cpu = dict(wl.ref)
     if args.ref_trials:
         for m, n in zip(("ic", "lt"), args.ref_trials):
             if m in wl.cpu:
@@ -963,7 +966,7 @@ def main():
                     help="run one counted step only (for ncu captures of its launches)")
     ap.add_argument("--ref-trials", type=int, nargs=2, default=None,
                     help="IC and LT trials per reference step (single-seed-set workloads; default: the "
-                         "workload's CPU-baseline sample)")
+                         "workload's reference sample, 8 + 8 on R-MAT scale 24: one trial per host thread)")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
