@@ -326,17 +326,24 @@ def oracle_sample(wl: Workload, first: int = 0):
     parts = []
     t0 = time.perf_counter()
     if wl.batch is None:
+        # the models' trials share one pool of host threads, one trial per job, so that the cores stay busy
+        # across both models (a large-graph trial is the unit of work here: tens of seconds on one core)
+        import concurrent.futures as cf
+        jobs = []
         for model in ("ic", "lt"):
             data = wl.models.get(model)
             if data is None:
                 continue
             n = wl.cpu[model]
             kw = {"ic_prob": data} if model == "ic" else {"lt_weight": data}
-            r = oracle.simulate_threads(model, wl.g, wl.seeds, n, wl.rng_seed, threads=cores, level_counts_len=0,
-                                        first_trial=first, **kw)
-            checks += r.edge_checks
+            jobs += [(model, first + j, kw) for j in range(n)]
             trials += n
             parts.append(f"{model.upper()} trials {first}..{first + n - 1}")
+        oracle.lib()
+        with cf.ThreadPoolExecutor(max_workers=max(1, min(cores, len(jobs)))) as ex:
+            res = list(ex.map(lambda j: oracle.simulate(j[0], wl.g, wl.seeds, 1, wl.rng_seed, first_trial=j[1],
+                                                        level_counts_len=0, **j[2]), jobs))
+        checks = sum(r.edge_checks for r in res)
     else:
         seed_off, seeds, tr, keys = wl.batch
         for i in range(wl.cpu["items"]):
