@@ -915,6 +915,25 @@ def run_ours(args):
             roof, alu = dict(alu, traffic=roof["traffic"], hbm_view={k: roof[k] for k in ("achieved", "peak",
                                                                                      "unit", "frac")}), roof
 
+    # the LT counting push is a stream of scattered 8-byte reads (the target's word of vis) and atomics
+    # (counter-plane toggles): its ceiling is the device's rate of such accesses, measured here for
+    # uniformly random words of an L2-resident region (32 MiB) and of a DRAM-resident one (4 GiB)
+    rnd = None
+    if "lt" in kern and kern["lt"]["kernel"] == "k_push<2>" and exp_ms["lt"] > 0:
+        KL = kern["lt"]
+        cl = KL["counted_call"]
+        per_s = mchecks["lt"] / max(1, cl["edge_checks"]) / (exp_ms["lt"] * 1e-3)
+        reads, atomics = cl["word_checks"] * per_s / 1e9, cl["updates"] * per_s / 1e9
+        rates = {f"{where}_{op}": P.cnd_random_access_rate(nbytes, op)[0] / 1e9
+                 for where, nbytes in (("l2", 32 << 20), ("dram", 4 << 30)) for op in ("read", "atomic")}
+        rnd = {"kernel": KL["kernel"], "unit": "G ops/s", "reads": reads, "atomics": atomics, "measured": rates,
+               "l2_time_frac": reads / rates["l2_read"] + atomics / rates["l2_atomic"],
+               "dram_time_frac": reads / rates["dram_read"] + atomics / rates["dram_atomic"],
+               "note": "reads = word checks, atomics = counter-plane toggles (activations not counted) per "
+                       "second of the kernel; *_time_frac = the share of the kernel's time the same accesses "
+                       "take at the measured uniformly random rates (cnd_random_access_rate): L2-resident is "
+                       "the ceiling, DRAM-resident the floor"}
+
     cpu = None if args.no_cpu_baseline else cpu_baseline(wl)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -935,6 +954,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roof,
         "roofline_other": alu,
+        "random_access": rnd,
         "kernels": kern,
         "cpu_baseline": cpu,
         "wall_s_timed_region": wall,

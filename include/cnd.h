@@ -476,6 +476,23 @@ cnd_status cnd_philox4x32_10(uint64_t rng_seed, const uint32_t *ctr, int64_t cou
 cnd_status cnd_philox_rate(int32_t iters, void *stream, double *blocks_per_s_out, double *ms_out);
 
 /*
+ * Rate of random 8-byte memory operations on the current device, the ceiling of the
+ * expansion kernels' scattered target-word accesses (measurement only; the paper has no
+ * counterpart).  Allocates a region of the largest power of two of 8-byte words that fits
+ * in region_bytes (zeroed; freed before return).  One launch of as many 256-thread blocks
+ * as are resident on all SMs; each thread makes iters accesses at uniformly random words
+ * of the region, each address derived from the value the previous access returned.
+ * op 0: 8-byte reads through L2 (ld.global.cg); op 1: 8-byte atomic XOR with return.
+ * A region well inside L2 (e.g. 32 MiB) gives the L2 rate, one far above it (e.g.
+ * 4 GiB) the DRAM rate.  Timed with CUDA events on `stream` (NULL = legacy default
+ * stream) after one short warm-up launch.  *ops_per_s_out = accesses per second;
+ * ms_out (may be NULL) = the launch time.  region_bytes >= 64, iters >= 1 (about 256
+ * keeps the launch in milliseconds); CND_ENOMEM if the region cannot be allocated.
+ */
+cnd_status cnd_random_access_rate(int64_t region_bytes, int32_t op, int32_t iters, void *stream,
+                                  double *ops_per_s_out, double *ms_out);
+
+/*
  * Allocation-free IC simulation.  The paper has no counterpart: this entry
  * point exists for callers that must not allocate device memory while a
  * simulation runs -- for example code that runs on a device whose memory is

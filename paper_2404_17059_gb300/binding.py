@@ -28,7 +28,7 @@ EXPORTS = (
     "cnd_lt_simulate_batch", "cnd_autotune", "cnd_im_opts_init", "cnd_ic_im_celf", "cnd_lt_im_celf",
     "cnd_sur_create", "cnd_sur_destroy", "cnd_sur_set_params", "cnd_sur_get_params", "cnd_sur_forward",
     "cnd_sur_loss_grad", "cnd_sur_adam", "cnd_sur_scores", "cnd_sur_train_opts_init", "cnd_sur_train",
-    "cnd_ic_im_screened", "cnd_sur_onehop", "cnd_philox_rate",
+    "cnd_ic_im_screened", "cnd_sur_onehop", "cnd_philox_rate", "cnd_random_access_rate",
 )
 CND_SUR_N_PARAMS = 18689
 
@@ -193,6 +193,8 @@ def load(build_if_missing: bool = True):
         L.cnd_philox4x32_10.restype = i32
         L.cnd_philox_rate.argtypes = [i32, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.cnd_philox_rate.restype = i32
+        L.cnd_random_access_rate.argtypes = [i64, i32, i32, vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.cnd_random_access_rate.restype = i32
         L.cnd_ic_simulate_noalloc.argtypes = [vp, vp, i32, i64, u64, vp, vp, vp]
         L.cnd_ic_simulate_noalloc.restype = i32
         L.cnd_last_error.argtypes = []
@@ -384,6 +386,18 @@ def cnd_philox_rate(iters=4096, stream=None):
     (returns (blocks_per_s, launch_ms))."""
     r, ms = C.c_double(), C.c_double()
     _check(load().cnd_philox_rate(int(iters), stream, C.byref(r), C.byref(ms)))
+    return r.value, ms.value
+
+
+RANDOM_OPS = {"read": 0, "atomic": 1}
+
+
+def cnd_random_access_rate(region_bytes, op="read", iters=256, stream=None):
+    """Measured random 8-byte reads ("read") or atomic XORs with return ("atomic") per second over a
+    device region of region_bytes (rounded down to a power of two); returns (ops_per_s, launch_ms)."""
+    r, ms = C.c_double(), C.c_double()
+    _check(load().cnd_random_access_rate(int(region_bytes), RANDOM_OPS[op], int(iters), stream, C.byref(r),
+                                         C.byref(ms)))
     return r.value, ms.value
 
 

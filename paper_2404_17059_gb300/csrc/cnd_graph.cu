@@ -84,6 +84,27 @@ __global__ void __launch_bounds__(256) k_philox_rate(RoundKeys rk, int32_t iters
     sink[t] = a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w;
 }
 
+// Random 8-byte accesses over a region of 2^k words (mask = 2^k - 1): each thread
+// follows one chain, the next address derived from the value the previous access
+// returned (a splitmix64 step, Steele, Lea and Flood 2014), so every access waits
+// for the one before it, as the expansion kernels' do.  OP 0: ld.global.cg read;
+// OP 1: atomic XOR with return.
+template <int OP>
+__global__ void __launch_bounds__(256) k_random_rate(unsigned long long *__restrict__ region, uint64_t mask,
+                                                     int32_t iters, uint64_t *__restrict__ sink) {
+    const uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    uint64_t x = t;
+    for (int32_t i = 0; i < iters; ++i) {
+        uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const uint64_t r = OP == 0 ? (uint64_t)__ldcg(region + (z & mask)) : (uint64_t)atomicXor(region + (z & mask), 1ull);
+        x += r;
+    }
+    sink[t] = x;
+}
+
 static void free_dev(cnd_graph_dev &d) {
     cudaFree(d.row_ptr);
     cudaFree(d.ic_edge);
@@ -399,6 +420,65 @@ cnd_status cnd_philox_rate(int32_t iters, void *stream, double *blocks_per_s_out
     } while (0);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
+    cudaFree(sink);
+    return rs;
+}
+
+cnd_status cnd_random_access_rate(int64_t region_bytes, int32_t op, int32_t iters, void *stream,
+                                  double *ops_per_s_out, double *ms_out) {
+    clear_error();
+    if (region_bytes < 64 || op < 0 || op > 1 || iters <= 0 || !ops_per_s_out) {
+        set_error("cnd_random_access_rate: bad arguments");
+        return CND_EINVAL;
+    }
+    uint64_t words = 8;
+    while (words * 2 <= (uint64_t)region_bytes / 8) words *= 2;
+    const void *fn = op == 0 ? (const void *)k_random_rate<0> : (const void *)k_random_rate<1>;
+    int dev = 0, sms = 0, per_sm = 0;
+    CND_CUDA_TRY(cudaGetDevice(&dev));
+    CND_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    CND_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0));
+    const int blocks = sms * std::max(per_sm, 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *region = nullptr;
+    uint64_t *sink = nullptr;
+    if (cudaMalloc(&region, words * 8) != cudaSuccess ||
+        cudaMalloc(&sink, sizeof(uint64_t) * 256 * (size_t)blocks) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(region);
+        set_error("cnd_random_access_rate: cannot allocate %llu bytes", (unsigned long long)(words * 8));
+        return CND_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cnd_status rs = CND_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaMemsetAsync(region, 0, words * 8, st)) != cudaSuccess || (e = cudaEventCreate(&e0)) != cudaSuccess ||
+            (e = cudaEventCreate(&e1)) != cudaSuccess) {
+            set_error("cnd_random_access_rate: %s", cudaGetErrorString(e));
+            rs = CND_ECUDA;
+            break;
+        }
+        const uint64_t mask = words - 1;
+        if (op == 0) k_random_rate<0><<<blocks, 256, 0, st>>>(region, mask, std::min(iters, 16), sink);  // warm-up
+        else k_random_rate<1><<<blocks, 256, 0, st>>>(region, mask, std::min(iters, 16), sink);
+        cudaEventRecord(e0, st);
+        if (op == 0) k_random_rate<0><<<blocks, 256, 0, st>>>(region, mask, iters, sink);
+        else k_random_rate<1><<<blocks, 256, 0, st>>>(region, mask, iters, sink);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        if ((e = cudaGetLastError()) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) {
+            set_error("cnd_random_access_rate: %s", cudaGetErrorString(e));
+            rs = CND_ECUDA;
+            break;
+        }
+        *ops_per_s_out = 256.0 * (double)blocks * (double)iters / (ms * 1e-3);
+        if (ms_out) *ms_out = ms;
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(region);
     cudaFree(sink);
     return rs;
 }

@@ -512,6 +512,142 @@ __global__ void __launch_bounds__(kBlock, MODE == 2 ? 4 : 6) k_finalize(Params p
     count_add(p, C_DRAWS, n_dr);
 }
 
+// Frontier collect when no word waits (tau = 0) and a node's words fit kCollectNq
+// dirty-mask words (B <= 256): every dirty word then holds new bits, so a node keeps
+// all of them.  A warp takes 32 listed nodes, one per lane, places their slots, pool
+// pairs and work items with one atomic each per 32 nodes, then its lanes go over the
+// 32 nodes' (word, bits) pairs and work items together, each lane finding the node of
+// its entry by a binary search of the warp's prefix sums.  No block barrier; the loads
+// of 32 nodes are in flight at once, and each lane issues the nxt loads of two pairs
+// before it stores either.  Same outputs as k_finalize<1> up to the order of the
+// slots, pairs and work items in the pool.
+constexpr int kCollectNq = 4;
+
+__device__ __forceinline__ int owner_of(const int *pre, int q) {  // largest j < 32 with pre[j] <= q
+    int j = 0;
+#pragma unroll
+    for (int step = 16; step >= 1; step >>= 1)
+        if (pre[j + step] <= q) j += step;
+    return j;
+}
+
+template <bool ONE_WORD>  // nq == 1
+__global__ void __launch_bounds__(kBlock) k_collect(Params p_) {
+    constexpr int kU = 2;  // pairs per lane whose loads go out together
+    Params p = p_;
+    resolve(p);
+    __shared__ int s_pp[kWarps][33], s_ip[kWarps][33];
+    __shared__ int s_v[kWarps][32], s_slot[kWarps][32], s_ne[kWarps][32];
+    __shared__ uint64_t s_dm[kWarps][kCollectNq][32];
+    const int lane = lane_id();
+    const int wid = threadIdx.x >> 5;
+    const int count = *p.lin_cnt;
+    const int B = p.B, nq = ONE_WORD ? 1 : p.nq;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int n_warps = (gridDim.x * blockDim.x) >> 5;
+    unsigned long long pc = 0;
+    if (lane == 0) {
+        s_pp[wid][0] = 0;
+        s_ip[wid][0] = 0;
+    }
+    for (int base = warp * 32; base < count; base += n_warps * 32) {
+        const int i = base + lane;
+        int v = 0, K = 0, deg = 0;
+        if (i < count) v = p.lin[i];
+        for (int q = 0; q < nq; ++q) {
+            uint64_t dm = 0;
+            if (i < count) {
+                uint64_t *d = p.dmask + (size_t)v * nq + q;
+                dm = *d;
+                if (dm) *d = 0ull;
+            }
+            s_dm[wid][q][lane] = dm;
+            K += __popcll(dm);
+        }
+        if (K) deg = p.row_ptr[v + 1] - p.row_ptr[v];
+        const int ne = edges_per_item(p, K);
+        const int hs = K > 0 ? 1 : 0;
+        const int nch = deg > 0 ? (deg + ne - 1) / ne : 0;
+        int sk = K, sh = hs, sc = nch, dg = deg;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a1 = __shfl_up_sync(kFull, sk, o), a2 = __shfl_up_sync(kFull, sh, o),
+                      a3 = __shfl_up_sync(kFull, sc, o);
+            if (lane >= o) {
+                sk += a1;
+                sh += a2;
+                sc += a3;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dg += __shfl_xor_sync(kFull, dg, o);
+        unsigned long long ps0 = 0;
+        int item0 = 0;
+        if (lane == 31) {
+            if (sk) ps0 = atomicAdd((unsigned long long *)p.out.cnt, ((unsigned long long)sh << 32) | (unsigned)sk);
+            if (sc) item0 = atomicAdd(&p.out.cnt[2], sc);
+        }
+        if (lane == 0 && dg) atomicAdd(&p.out.cnt[3], dg);
+        ps0 = __shfl_sync(kFull, ps0, 31);
+        item0 = __shfl_sync(kFull, item0, 31);
+        const int n_pairs = __shfl_sync(kFull, sk, 31), n_items = __shfl_sync(kFull, sc, 31);
+        const int pool0 = (int)(uint32_t)ps0;
+        const int slot = (int)(ps0 >> 32) + sh - hs;
+        if (K) {
+            p.out.node[slot] = v;
+            p.out.poff[slot] = pool0 + sk - K;
+            p.out.pk[slot] = K;
+        }
+        s_pp[wid][lane + 1] = sk;
+        s_ip[wid][lane + 1] = sc;
+        s_v[wid][lane] = v;
+        s_slot[wid][lane] = slot;
+        s_ne[wid][lane] = ne;
+        __syncwarp();
+        for (int q0 = 0; q0 < n_pairs; q0 += 32 * kU) {
+            uint64_t x[kU];
+            size_t idx[kU];
+            int w[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + 32 * u + lane;
+                x[u] = 0ull;
+                idx[u] = 0;
+                w[u] = 0;
+                if (q < n_pairs) {
+                    // the r-th listed word of node j
+                    const int j = owner_of(s_pp[wid], q);
+                    int r = q - s_pp[wid][j], qq = 0;
+                    uint64_t dm = s_dm[wid][0][j];
+                    while (!ONE_WORD && r >= __popcll(dm)) {
+                        r -= __popcll(dm);
+                        dm = s_dm[wid][++qq][j];
+                    }
+                    w[u] = 64 * qq + nth_set_bit(dm, r);
+                    idx[u] = (size_t)s_v[wid][j] * B + w[u];
+                    x[u] = __ldcg((const unsigned long long *)p.nxt + idx[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const int q = q0 + 32 * u + lane;
+                if (q < n_pairs) {
+                    p.nxt[idx[u]] = 0ull;
+                    p.out.pw[pool0 + q] = (uint16_t)w[u];
+                    p.out.pb[pool0 + q] = x[u];
+                    pc += __popcll(x[u]);
+                }
+            }
+        }
+        for (int q = lane; q < n_items; q += 32) {
+            const int j = owner_of(s_ip[wid], q);
+            p.out.work[item0 + q] = make_int2(s_slot[wid][j], (q - s_ip[wid][j]) * s_ne[wid][j]);
+        }
+        __syncwarp();
+    }
+    add_level_count(p, pc);
+}
+
 // ---------------------------------------------------------------- LT counting form
 // Set-up of a pass in the counting form (every node's non-zero in-weights equal w_v).  With k
 // active in-neighbours, v activates iff k * w_v > theta, i.e. iff k > q = floor(theta / w_v).
@@ -1418,9 +1554,13 @@ static cnd_status run_items(int model, const cnd_graph_dev &G, const char *fn, s
     const void *k_fin_uk = model == 0 ? (const void *)k_finalize<1, false>
                            : lt_cnt   ? (const void *)k_finalize<1, false>
                                       : (const void *)k_finalize<2, false>;
+    // nothing waits and a node's words fit one dirty-mask word: the barrier-free collect
+    const bool flat = P.tau == 0 && nq <= kCollectNq;
+    const void *k_col = nq == 1 ? (const void *)k_collect<true> : (const void *)k_collect<false>;
+    if (flat && (model == 0 || lt_cnt)) k_fin_pw = k_fin_uk = k_col;
     const void *k_init_pw = (const void *)k_lt_init<true>, *k_init_uk = (const void *)k_lt_init<false>;
     const int init_blocks = G.num_sms * resident_blocks(k_init_uk);
-    const void *k_seedfin = (const void *)k_finalize<1, false>;
+    const void *k_seedfin = nq <= kCollectNq ? k_col : (const void *)k_finalize<1, false>;
     const int push_blocks = G.num_sms * resident_blocks(k_push_uk);
     const void *k_pull_pw = (const void *)k_pull_ic<true>, *k_pull_uk = (const void *)k_pull_ic<false>;
     const int pull_blocks = G.num_sms * resident_blocks(k_pull_uk);

@@ -117,3 +117,15 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "libcnd.so"))
     with pytest.raises(RuntimeError, match="not built"):
         binding.load(build_if_missing=False)
+
+
+def test_measurement_probes_reject_bad_arguments_on_host():
+    """The rate probes check their arguments on the host, before any CUDA call."""
+    import ctypes
+    L = binding.load()
+    r, ms = ctypes.c_double(), ctypes.c_double()
+    for region, op, iters in ((32, 0, 16), (1 << 20, 2, 16), (1 << 20, -1, 16), (1 << 20, 0, 0)):
+        assert L.cnd_random_access_rate(region, op, iters, None, ctypes.byref(r), ctypes.byref(ms)) == P.CND_EINVAL
+    assert L.cnd_random_access_rate(1 << 20, 0, 16, None, None, None) == P.CND_EINVAL
+    assert "bad arguments" in P.cnd_last_error()
+    assert L.cnd_philox_rate(0, None, ctypes.byref(r), None) == P.CND_EINVAL
