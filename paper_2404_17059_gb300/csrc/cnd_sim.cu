@@ -223,7 +223,11 @@ struct ListBuf {
 
     // List v once per step (the stamp in mark[v] says whether it already is).
     __device__ __forceinline__ void add(const Params &p, bool want, int v) {
-        const bool need = want && __ldcg(&p.mark[v]) != p.stamp && atomicExch(&p.mark[v], p.stamp) != p.stamp;
+        put(p, want && __ldcg(&p.mark[v]) != p.stamp && atomicExch(&p.mark[v], p.stamp) != p.stamp, v);
+    }
+
+    // Append v for the lanes with need set (the caller has claimed mark[v] for this step).
+    __device__ __forceinline__ void put(const Params &p, bool need, int v) {
         const unsigned nm = __ballot_sync(kFull, need);
         if (nm) {
             if (need) buf[n + __popc(nm & ((1u << lane_id()) - 1u))] = v;
@@ -788,7 +792,7 @@ __global__ void __launch_bounds__(kBlock, kPushMinBlocks) k_push(Params p_) {
         const uint32_t magic = 0xFFFFFFFFu / (uint32_t)k + 1u;
         for (uint32_t t0 = 0; t0 < T; t0 += 32) {
             const uint32_t t = t0 + lane;
-            bool hit = false;
+            bool hit = false, claimed = false;  // claimed: this lane took mark[v] for the step
             int v = 0;
             uint64_t ic_c = 0;
             uint32_t ic_thr = 0;
@@ -831,9 +835,11 @@ __global__ void __launch_bounds__(kBlock, kPushMinBlocks) k_push(Params p_) {
                                 carry &= (uint64_t)atomicXor(pl + i, (unsigned long long)carry);
                             }
                             if (carry) {
+                                // the update of nxt and the claim of the node's listing go out together
                                 atomicOr((unsigned long long *)p.vis + idx, (unsigned long long)carry);
                                 const uint64_t old =
                                     atomicOr((unsigned long long *)p.nxt + idx, (unsigned long long)carry);
+                                claimed = atomicExch(&p.mark[v], p.stamp) != p.stamp;
                                 mark_dirty(p, v, w, old);
                                 hit = true;
                             }
@@ -953,13 +959,15 @@ __global__ void __launch_bounds__(kBlock, kPushMinBlocks) k_push(Params p_) {
                     // step has just set are or-ed again into nxt, which is idempotent
                     atomicOr((unsigned long long *)p.vis + ic_idx, (unsigned long long)nb);
                     const uint64_t old = atomicOr((unsigned long long *)p.nxt + ic_idx, (unsigned long long)nb);
+                    claimed = atomicExch(&p.mark[ic_v], p.stamp) != p.stamp;
                     mark_dirty(p, ic_v, ic_w, old);
                     ++n_up;
                     hit = true;
                 }
                 __syncwarp();
             }
-            lb.add(p, hit, v);
+            if (MODEL == 1) lb.add(p, hit, v);
+            else lb.put(p, claimed, v);
         }
         __syncwarp();
     }
