@@ -33,9 +33,11 @@
 //              (counting form: one bit-sliced increment of v's counter word by
 //              the trials of f & ~vis_v[w]; a carry out of the top plane is
 //              the activation, see k_lt_init)
-//   finalize   per listed node: IC takes the dirty words of nxt; LT draws the
-//              thresholds of the touched trials and activates where
-//              acc > theta; the non-empty words become the next frontier
+//   collect    per listed node: IC and the LT counting form take the dirty
+//              words of nxt (k_collect; k_finalize where words wait); the LT
+//              accumulate form draws the thresholds of the touched trials and
+//              activates where acc > theta (k_finalize<2>); the non-empty
+//              words become the next frontier
 // then the per-trial spread and per-node counts are reduced from vis.
 #include <cuda_runtime.h>
 #include <stdio.h>
@@ -53,10 +55,11 @@
 namespace cnd {
 
 constexpr int kMaxB = 2048;  // words per node per pass (dirty mask: one 64-bit word per lane)
-// Occupancy of the two step kernels (both latency-bound on scattered word traffic): the push
-// runs 8 blocks of 256 threads per SM (32 registers), the finalize 6 (IC) or 4 (LT, which
-// converts accumulator rows and needs more registers).  Measured on GB300: against one block
-// minimum, BA n=100k IC -21 %, LT -15 %, a sparse 256-set batch -17 %.
+// Occupancy of the step kernels (all latency-bound on scattered word traffic): the push runs
+// 8 blocks of 256 threads per SM (32 registers), k_collect 6, the block-cooperative finalize
+// 6 (IC) or 4 (LT accumulate form, which converts accumulator rows and needs more registers).
+// Measured on GB300: against one block minimum, BA n=100k IC -21 %, LT -15 %, a sparse
+// 256-set batch -17 %.
 constexpr int kPushMinBlocks = 8;
 constexpr int kStageB = 64;  // pairs of a push work item staged in shared memory (more: read from the pool)
 constexpr int kPullMaxB = 256;  // words per node the pull kernel keeps in registers
@@ -205,7 +208,7 @@ __device__ __forceinline__ uint64_t word_g0(const Params &p, int w) {
     return PERWORD ? p.wg0[w] : p.g_base + 16ull * (uint64_t)w;
 }
 
-// Per-warp staging of the nodes a push lists for the finalize kernel: one
+// Per-warp staging of the nodes a push lists for the collect / finalize kernel: one
 // global atomic per 32 or more nodes instead of one per warp iteration.
 struct ListBuf {
     int32_t *buf;  // 64 entries in shared memory
@@ -2440,7 +2443,10 @@ static cnd_status simulate_noalloc(const cnd_graph *g, const int32_t *seeds, int
         CND_CUDA_TRY(cudaMemsetAsync(P.nxt, 0, sizeof(uint64_t) * nB, st));
         CND_CUDA_TRY(cudaMemsetAsync(P.dmask, 0, sizeof(uint64_t) * (size_t)n * nq, st));
         const void *k_push_fn = (const void *)k_push<0, false>;
-        const void *k_fin_fn = (const void *)k_finalize<1, false>;
+        // nothing waits here (tau = 0): the barrier-free collect where a node's words fit its masks
+        const void *k_fin_fn = nq == 1 ? (const void *)k_collect<true>
+                               : nq <= kCollectNq ? (const void *)k_collect<false>
+                                                  : (const void *)k_finalize<1, false>;
         const int push_blocks = G.num_sms * resident_blocks(k_push_fn);
         const int fin_blocks = G.num_sms * resident_blocks(k_fin_fn);
         uint64_t desc[2 * kMaxB + 2];  // valid[B] | wout[B] | one seed run
