@@ -9,6 +9,9 @@ The oracle cannot run every trial at this size, so:
 
 - sampled trials are recomputed one by one (``first_trial = t``, one trial each) and their spreads
   must be identical -- trial ids at word, lane and pass boundaries and at the top of the 100,000;
+- four trials per model are also run alone on the GPU (one-trial calls) and every output of each is
+  compared with the oracle's: the activated set over all n nodes, the edge checks, the activations
+  per step;
 - the outputs no sample can check are tied by identities that hold at any size: the per-node counts
   sum to the summed spreads (both count the (trial, active node) pairs), edge checks equal the sum of
   out-degree times per-node count (the oracle's definition: out-edges of every active node in every
@@ -98,6 +101,34 @@ def test_rmat24_bench_step_sampled_trials(rmat24, model):
     local = np.unique(np.concatenate([[0, 1, 63, 64, 511, 512, 1023], rng.integers(0, T, 9)]))
     want = _oracle_trials(model, g, seeds, 1, first + local, p=p, w=w)
     assert np.array_equal(spread[local], want), (local, spread[local], want)
+
+
+@pytest.mark.parametrize("model", ["ic", "lt"])
+def test_rmat24_single_trials_every_output(rmat24, model):
+    """Four trials of the configuration, each run alone on the GPU (first_trial = t, one trial), against
+    the oracle's run of the same trial: the activated set over all 16.7 M nodes (per-node counts of the
+    one trial), the edge checks and the activations per step are identical."""
+    g, G, p, w, seeds = rmat24
+    ts, L = (0, 64, 50_048, 99_968), 1024  # a call's first trial is a multiple of 64
+    f = P.cnd_ic_simulate_ex if model == "ic" else P.cnd_lt_simulate_ex
+    got = []
+    for t in ts:
+        r = f(G, torch.as_tensor(seeds, device="cuda"), 1, 1, first_trial=t, edge_checks=True, level_counts_len=L)
+        torch.cuda.synchronize()
+        assert r.status == P.CND_OK
+        got.append((r.node_count.cpu().numpy(), r.edge_checks, r.level_counts.cpu().numpy()))
+
+    def one(t):
+        return oracle.simulate(model, g, seeds, 1, 1, ic_prob=p, lt_weight=w, first_trial=int(t), level_counts_len=L)
+
+    with cf.ThreadPoolExecutor(max_workers=len(ts)) as ex:
+        want = list(ex.map(one, ts))
+    for t, (count, checks, levels), o in zip(ts, got, want):
+        assert o.status >= 0
+        assert np.array_equal(count, o.node_count), t
+        assert checks == o.edge_checks, (t, checks, o.edge_checks)
+        assert np.array_equal(levels, o.level_counts), t
+        assert levels[L - 1] == 0  # every cascade ended within the recorded steps
 
 
 def test_rmat24_lt_two_passes(rmat24):
