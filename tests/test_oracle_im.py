@@ -51,7 +51,7 @@ def test_greedy_against_exhaustive_search():
     seeds, f = im.greedy("ic", g, 2, T, 5, ic_prob=p)
     best = max(_F("ic", g, list(X), T, 5, ic_prob=p) for X in itertools.combinations(range(g.n), 2))
     best1 = max(_F("ic", g, [v], T, 5, ic_prob=p) for v in range(g.n))
-    assert f[0] == best1                              # round 1 of greedy is exact
+    assert f[0] == best1                              # the first greedy pick is exact
     assert best >= f[1] >= (1 - (1 - 1 / 2) ** 2) * best  # k=2 greedy bound 1-(1-1/k)^k
 
 
